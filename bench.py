@@ -1,0 +1,334 @@
+"""Benchmark: f + grad evaluations per second of Alg. 2 (fg_implicit) on one GB300.
+
+Workload (one "step" = one full evaluation, the fused pass over V plus the model terms):
+    n = 256 features, d = 4, r = 16, p = 2^24 Gaussian-mixture samples (16 unit-norm means,
+    Dirichlet(1) weights, sigma = 0.1), nu = 1/p, V stored in BF16 (8.6 GB, far larger than
+    L2, so no flush is needed between steps). The same samples in FP32 are timed beside it.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on the host cores
+instead, on a bounded sample of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FEAT, D, R, P_FULL, SIGMA, N_MEANS, SEED = 256, 4, 16, 1 << 24, 0.1, 16, 2024
+WORKLOAD = "gmm_n256_d4_r16_p16777216"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        return dict(hbm_gbs=pk["hbm_gbs"], src="measured")
+    return dict(hbm_gbs=6800.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fg_tc.cu", "fg_simt.cu"):
+        p = os.path.join(ROOT, "paper_1911_03813_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        t = json.load(open(path)).get(kernel_tag)
+    except ValueError:
+        return None
+    if not t or t.get("source_hash") != kernel_source_hash():
+        return None
+    return t.get("dram_bytes_per_launch_full")
+
+
+def cpu_baseline(seconds=12.0, p_sample=1 << 17):
+    """The FP64 oracle (NumPy, host BLAS threads) on a bounded sample of the workload, scaled to
+    full-workload evaluations per second."""
+    import numpy as np
+
+    import oracle
+    from paper_1911_03813_gb300 import inputs
+    data = inputs.gmm(N_FEAT, p_sample, N_MEANS, SIGMA, seed=SEED)
+    Vt = np.ascontiguousarray(data["V"].T)
+    lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
+    oracle.fg_implicit(None, Vt, lam, A, D)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.fg_implicit(None, Vt, lam, A, D)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    per_eval_sample = el / k
+    per_eval_full = per_eval_sample * (P_FULL / p_sample)
+    cores = len(os.sched_getaffinity(0))
+    return dict(value=1.0 / per_eval_full, unit="evals/s", cores=cores, kind="oracle",
+                sample="%d of %d samples (n=%d, d=%d, r=%d), %d evaluations in %.1f s, scaled "
+                       "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    import numpy as np
+
+    import oracle
+    from paper_1911_03813_gb300 import inputs
+    p_sample = 1 << 16
+    data = inputs.gmm(N_FEAT, p_sample, N_MEANS, SIGMA, seed=SEED)
+    Vt = np.ascontiguousarray(data["V"].T)
+    lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
+    for _ in range(warm):
+        oracle.fg_implicit(None, Vt, lam, A, D)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.fg_implicit(None, Vt, lam, A, D)
+    el = time.perf_counter() - t0
+    per_full = el / steps * (P_FULL / p_sample)
+    v = 1.0 / per_full
+    line = {"impl": "reference", "metric": "f+grad evaluations/s", "value": v,
+            "unit": "evals/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "storage": "f64 (oracle)",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle",
+                             "sample": "%d of %d samples per step, scaled by p" % (p_sample, P_FULL)},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p", type=int, default=P_FULL)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_03813_gb300 import inputs, stmf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    P = args.p
+    st32 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="f32")
+    st16 = dict(st32)
+    st16["data"] = st32["data"].to(torch.bfloat16)
+    st16["dtype"] = "bf16"
+    st16["ld"] = inputs.padded_ld(N_FEAT, "bf16")
+    lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
+    lam_t = torch.tensor(lam, device=dev)
+    A_t = torch.tensor(A.T.copy(), device=dev).T
+    ctx = stmf.default_context(local)
+    stmf.reserve(st16, R)
+    stmf.reserve(st32, R)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    gl = torch.empty(R, dtype=torch.float64, device=dev)
+    GA = torch.empty((R, N_FEAT), dtype=torch.float64, device=dev).T
+    out = (f, gl, GA)
+    stream = torch.cuda.current_stream()
+
+    def timed(st, steps, warm, prof=False):
+        for _ in range(warm):
+            stmf.fg(st, None, D, lam_t, A_t, out=out)
+        if prof:
+            stmf.profile_enable(True, ctx=ctx)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            stmf.fg(st, None, D, lam_t, A_t, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        pass_ms = None
+        if prof:
+            tot, cnt = stmf.profile_read(ctx=ctx)
+            stmf.profile_enable(False, ctx=ctx)
+            pass_ms = tot / max(cnt, 1)
+        return ms, pass_ms
+
+    ms32, pass32 = timed(st32, max(args.steps // 2, 1), args.warmup, prof=True)
+    with ClockSampler(local) as clk:
+        ms16, pass16 = timed(st16, args.steps, args.warmup, prof=True)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms16, ms32], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms16, ms32 = t.tolist()
+    steps32 = max(args.steps // 2, 1)
+    value = world * args.steps / (ms16 / 1e3)
+    bytes16 = P * N_FEAT * 2
+    bytes32 = P * N_FEAT * 4
+    peaks = measured_peaks()
+    ach16 = bytes16 / (pass16 / 1e3) / 1e9
+    ach32 = bytes32 / (pass32 / 1e3) / 1e9
+
+    # end to end through the public API: pinned host V -> device, evaluate, read f and g back
+    e2e = None
+    if args.e2e_steps > 0:
+        host16 = torch.empty(st16["data"].shape, dtype=torch.bfloat16, pin_memory=True)
+        host16.copy_(st16["data"])
+        dev16 = torch.empty_like(st16["data"])
+        st_e = dict(st16)
+        st_e["data"] = dev16
+        lam_h = torch.tensor(lam).pin_memory()
+        A_h = torch.tensor(A.T.copy()).pin_memory()
+        res_h = torch.empty(1 + R + R * N_FEAT, dtype=torch.float64).pin_memory()
+        res_d = torch.empty(1 + R + R * N_FEAT, dtype=torch.float64, device=dev)
+        A_d = torch.empty((R, N_FEAT), dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            dev16.copy_(host16, non_blocking=True)
+            lam_t.copy_(lam_h, non_blocking=True)
+            A_d.copy_(A_h, non_blocking=True)
+            stmf.fg(st_e, None, D, lam_t, A_d.T, out=(res_d[0:1], res_d[1:1 + R],
+                                                        res_d[1 + R:].view(R, N_FEAT).T))
+            res_h.copy_(res_d, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": world * args.e2e_steps / el, "unit": "evals/s",
+               "h2d_bytes_per_step": bytes16 + 8 * (R + R * N_FEAT),
+               "d2h_bytes_per_step": 8 * (1 + R + R * N_FEAT)}
+        del host16, dev16
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    traffic = ncu_traffic("fg_pass_bf16")
+    line = {
+        "metric": "f+grad evaluations/s (BF16 V; FP32 V beside it)",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms16 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD if P == P_FULL else "gmm_n256_d4_r16_p%d" % P,
+                   "n": N_FEAT, "d": D, "r": R, "p": P, "sigma": SIGMA,
+                   "l2": "inputs larger than L2 (8.6 GB BF16 per step)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "hbm_gbs_over_V": bytes16 / (ms16 / args.steps / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": ach16, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": ach16 / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "fused pass (Alg. 2 line 2)", "peak_src": peaks["src"],
+                     "algorithmic_bytes_per_launch": bytes16},
+        "fp32": {"value": steps32 / (ms32 / 1e3) * world, "unit": "evals/s",
+                 "ms_per_step": ms32 / steps32, "hbm_gbs_over_V": bytes32 / (ms32 / steps32 / 1e3) / 1e9,
+                 "pass_frac_of_hbm": ach32 / peaks["hbm_gbs"],
+                 "bf16_over_fp32": (args.steps / ms16) / (steps32 / ms32)},
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * (args.steps + max(args.steps // 2, 1)),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * stmf.h -- C ABI of the GB300 library for implicit symmetric CP fitting of moment tensors.
+ *
+ * The method (Sherman & Kolda, "Estimating Higher-Order Moments Using Symmetric Tensor
+ * Decomposition", arXiv 1911.03813) fits a rank-r symmetric model
+ *     M = sum_j lambda_j a_j^{(x)d}                                   (Sec. 1, eq. cp_element)
+ * to the d-th moment tensor of p weighted samples
+ *     X = sum_l nu_l v_l^{(x)d}                                       (Sec. 3, eq. tensorX)
+ * by minimising f = ||X - M||^2 (Sec. 2.6, eq. optFunc) without ever forming X: the function
+ * and gradient come from Alg. 2 (fg_implicit, Sec. 3.4), whose cost is one pass over the
+ * samples.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Memory: every array argument is a DEVICE pointer on the context's device unless the
+ *    comment says "host". The caller owns all arrays it passes; the library never frees them.
+ *    The library owns only its context (and the workspace the context allocates).
+ *  - Layouts: the sample matrix V (the paper's n x p, one sample per column) is stored
+ *    sample-major: p rows of `ld` elements, row l holding v_l in its first n entries (V stored
+ *    column-major with leading dimension ld). The factor matrix A (n x r) is column-major with
+ *    leading dimension n; G_A has the same layout. lambda and g_lambda hold r entries.
+ *    All model parameters and outputs are FP64.
+ *  - Errors: every call returns an stmf_status and never throws. Arguments are validated on
+ *    the host before anything is launched; on a validation error nothing is launched and
+ *    stmf_last_error() describes the failing argument. Kernel launch failures return
+ *    STMF_ECUDA. Errors found on the device (a non-finite result, a bounded wait that ran out)
+ *    are recorded in the context's device status word and surface through
+ *    stmf_device_status().
+ *  - Asynchrony: stmf_fg and stmf_norm_x only enqueue work on `stream` (NULL = the legacy
+ *    default stream) and return; their outputs are valid once the stream reaches that point.
+ *  - Threads and streams: a context may be used from one host thread at a time, and calls on
+ *    different streams that share a context must not overlap on the device (they share the
+ *    context's workspace). Use one context per concurrent stream.
+ *  - Workspace: a context allocates its device workspace on first use and grows it when a call
+ *    needs more. A call that grows it synchronises the device, so make the first call of each
+ *    shape (or stmf_reserve) before capturing a CUDA graph.
+ */
+#ifndef STMF_H
+#define STMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* stmf_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  STMF_OK = 0,
+  STMF_EINVAL = 1,      /* an argument is out of range or misaligned */
+  STMF_ENOMEM = 2,      /* device allocation failed, or a request exceeds the memory budget */
+  STMF_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  STMF_ETIMEOUT = 4,    /* a bounded device wait ran out */
+  STMF_ENONFINITE = 5,  /* a result is NaN or infinite */
+  STMF_ENOTREADY = 6,   /* the request is still running */
+  STMF_ECANCELLED = 7,  /* the request was cancelled */
+  STMF_EBUSY = 8,       /* no slot free */
+  STMF_EUNSUPPORTED = 9 /* the device is not a GB300-class part (sm_103) */
+} stmf_status;
+
+typedef enum {
+  STMF_F64 = 0,  /* IEEE binary64 */
+  STMF_F32 = 1,  /* IEEE binary32 */
+  STMF_BF16 = 2, /* bfloat16 */
+  STMF_E4M3 = 3  /* OCP FP8 E4M3 with one FP32 scale per sample: v_l = scale[l] * q_l */
+} stmf_dtype;
+
+/* The samples V (the paper's n x p data matrix, Sec. 3), stored sample-major. */
+typedef struct {
+  const void* data;   /* device; p rows of ld elements of `dtype`; 16-byte aligned */
+  const float* scale; /* device; p FP32 per-sample scales for STMF_E4M3, else NULL */
+  int64_t n;          /* features per sample, 1 <= n <= 256 */
+  int64_t p;          /* number of samples, p >= 1 */
+  int64_t ld;         /* row stride in elements, ld >= n, ld * sizeof(dtype) % 16 == 0 */
+  int32_t dtype;      /* stmf_dtype */
+  int32_t reserved;
+} stmf_samples;
+
+typedef struct stmf_ctx* stmf_ctx_t;
+
+/* Library version, as 10000*major + 100*minor + patch. */
+int stmf_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* stmf_status_string(int status);
+
+/* Create a context on CUDA device `device`. Fails with STMF_EUNSUPPORTED when the device is
+ * not compute capability 10.3 (the kernels are built for sm_103a only). *out is set on
+ * success. */
+stmf_status stmf_create(int device, stmf_ctx_t* out);
+
+/* Destroy a context and free its workspace. Synchronises the device. NULL is accepted. */
+stmf_status stmf_destroy(stmf_ctx_t ctx);
+
+/* Text describing the last error returned on this context (static per context; valid until
+ * the next call on it). */
+const char* stmf_last_error(stmf_ctx_t ctx);
+
+/* Grow the workspace so that stmf_fg / stmf_norm_x on V with rank r need no allocation.
+ * Synchronises the device when it allocates. */
+stmf_status stmf_reserve(stmf_ctx_t ctx, const stmf_samples* V, int64_t r);
+
+/* Read the device status word (STMF_OK or the first device-side error since the last read),
+ * waiting for `stream`, and reset it to STMF_OK. *out_host is a host pointer. */
+stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, int32_t* out_host);
+
+/*
+ * stmf_fg -- function value and gradient by Alg. 2 (fg_implicit, Sec. 3.4):
+ *     Y   = V D_nu [V^T A]^{d-1}            (line 2, Lemma 3.3, eq. Y)
+ *     w_j = a_j^T y_j                       (line 3, Lemma 3.5: <X, M> = w^T lambda)
+ *     B = A^T A, C = B^{d-1}, u = (B * C) lambda   (lines 4-6, Lemma 3.4: ||M||^2 = lambda^T u)
+ *     f   = alpha + lambda^T u - 2 w^T lambda     (line 7)
+ *     g_lambda = -2 (w - u)                        (line 8, eq. gradl)
+ *     G_A = -2 d (Y - A D_lambda C) D_lambda       (line 9, eq. gradb)
+ * Powers of matrices are element-wise (Sec. 2).
+ *
+ *  V        samples (see stmf_samples). BF16 and E4M3 samples are contracted on the tensor
+ *           cores with FP32 accumulation; F32 with FP32 FMA; F64 with FP64 FMA. Per-block
+ *           partial sums are combined in FP64 and lines 3-9 run in FP64.
+ *  nu       device, p FP64 positive sample weights (Sec. 3 allows any positive vector), or NULL
+ *           for the paper's default nu_l = 1/p.
+ *  d        tensor order, 2 <= d <= 8 (d = 2 is the matrix case).
+ *  r        rank, 1 <= r <= 64.
+ *  lambda   device, r FP64.             A  device, n x r FP64 column-major (lda = n).
+ *  alpha    device pointer to the FP64 constant alpha = ||X||^2 (e.g. from stmf_norm_x), or NULL
+ *           for alpha = 0 (the shifted objective, Sec. 3.4).
+ *  f        device, 1 FP64 (out).   g_lambda  device, r FP64 (out).   G_A  device, n x r (out).
+ * Outputs may not alias inputs. Enqueued on `stream`; asynchronous.
+ */
+stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+                    int64_t r, const double* lambda, const double* A, const double* alpha,
+                    double* f, double* g_lambda, double* G_A, stmf_stream_t stream);
+
+/*
+ * stmf_norm_x -- alpha = ||X||^2 = nu^T (V^T V)^d nu, Lemma 3.4 applied to X (Sec. 3.3), the
+ * O(n p^2) constant of Alg. 2. Evaluated over the upper triangle of sample-tile pairs without
+ * forming the p x p Gram matrix; per-tile sums are combined in FP64.
+ *  V, nu, d   as for stmf_fg.     alpha_out  device, 1 FP64 (out).
+ * Enqueued on `stream`; asynchronous.
+ */
+stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+                        double* alpha_out, stmf_stream_t stream);
+
+/*
+ * Kernel timing for benchmarks (not part of the method). While enabled, every stmf_fg records
+ * a pair of CUDA events around its fused pass over V, on the call's stream. stmf_profile_read
+ * waits for the recorded events, returns the summed pass time in milliseconds and the number of
+ * passes (host pointers), and clears the record. At most 65536 passes are recorded.
+ */
+stmf_status stmf_profile_enable(stmf_ctx_t ctx, int32_t enable);
+stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* count_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STMF_H */

@@ -1,0 +1,273 @@
+// Fused pass over the samples on the CUDA cores (FP64 and FP32 storage; also BF16/E4M3 for
+// shapes the tensor-core pass does not take).
+//
+// One persistent block walks sample tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... and
+// accumulates, for its tiles only,
+//     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l^T      (Alg. 2 line 2, Lemma 3.3, eq. Y)
+//     w_part = sum_l nu_l (v_l^T A)^d                (Lemma 3.5: w_j = X a_j^d = a_j^T y_j)
+// Each tile is staged in shared memory once and used twice: phase 1 forms Z = V_tile A and the
+// weighted powers W = D_nu Z^{d-1}; phase 2 adds V_tile^T W into register accumulators. FP32
+// accumulators are folded into the block's FP64 partial slot every `flush_tiles` tiles, so an
+// FP32 sum never runs over more than flush_tiles * 64 samples. Partials are combined across
+// blocks in FP64 by the model-terms kernel in a fixed order (deterministic results).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "stmf_internal.h"
+
+namespace stmf {
+namespace {
+
+constexpr int TS = 64;      // samples per tile
+constexpr int NT = 256;     // threads per block
+constexpr int MAXACC = 64;  // Y accumulators per thread
+
+template <int DT>
+struct Storage;
+template <>
+struct Storage<STMF_F64> { using T = double; };
+template <>
+struct Storage<STMF_F32> { using T = float; };
+template <>
+struct Storage<STMF_BF16> { using T = __nv_bfloat16; };
+template <>
+struct Storage<STMF_E4M3> { using T = __nv_fp8_e4m3; };
+
+template <typename TC>
+__device__ __forceinline__ TC widen(double x) { return (TC)x; }
+template <typename TC>
+__device__ __forceinline__ TC widen(float x) { return (TC)x; }
+template <typename TC>
+__device__ __forceinline__ TC widen(__nv_bfloat16 x) { return (TC)__bfloat162float(x); }
+template <typename TC>
+__device__ __forceinline__ TC widen(__nv_fp8_e4m3 x) { return (TC)(float)x; }
+
+template <typename TC>
+__device__ __forceinline__ TC ipow(TC z, int e) {
+  TC t = z;
+  for (int k = 1; k < e; ++k) t *= z;
+  return e == 0 ? (TC)1 : t;
+}
+
+__host__ __device__ inline int vstride_of(int n) { return (n % 2 == 0) ? n + 1 : n; }
+
+template <typename TC>
+size_t smem_bytes(int n, int rp) {
+  auto up16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  size_t b = up16(sizeof(TC) * size_t(n) * rp);          // As[n][rp]
+  b += up16(sizeof(TC) * size_t(TS) * vstride_of(n));    // Vs[TS][vstride]
+  b += up16(sizeof(TC) * size_t(TS) * rp);               // Ws[TS][rp]
+  b += up16(sizeof(TC) * TS);                            // nus[TS]
+  b += up16(sizeof(double) * (NT / 32) * 16);            // wsh[warps][16]
+  return b;
+}
+
+template <typename TC, int DT, int JB>
+__global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
+  using TS_t = typename Storage<DT>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = prm.n, r = prm.r, rp = prm.r_pad, d = prm.d, ld = prm.ld;
+  const int vst = vstride_of(n);
+  auto up16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  unsigned char* ptr = smem_raw;
+  TC* As = reinterpret_cast<TC*>(ptr);
+  ptr += up16(sizeof(TC) * size_t(n) * rp);
+  TC* Vs = reinterpret_cast<TC*>(ptr);
+  ptr += up16(sizeof(TC) * size_t(TS) * vst);
+  TC* Ws = reinterpret_cast<TC*>(ptr);
+  ptr += up16(sizeof(TC) * size_t(TS) * rp);
+  TC* nus = reinterpret_cast<TC*>(ptr);
+  ptr += up16(sizeof(TC) * TS);
+  double* wsh = reinterpret_cast<double*>(ptr);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const TS_t* V = reinterpret_cast<const TS_t*>(prm.V);
+  double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+
+  // A (FP64, n x r column-major) -> As[i][j] in the compute type, zero-padded to rp columns.
+  for (int e = tid; e < n * rp; e += NT) {
+    const int i = e / rp, j = e - i * rp;
+    As[e] = j < r ? (TC)prm.A[i + size_t(n) * j] : (TC)0;
+  }
+  for (int e = tid; e < (NT / 32) * 16; e += NT) wsh[e] = 0.0;
+
+  const int nJB = rp / JB;
+  const int n_items = n * nJB;
+  constexpr int ITEMS = MAXACC / JB;
+  TC acc[MAXACC];
+#pragma unroll
+  for (int k = 0; k < MAXACC; ++k) acc[k] = (TC)0;
+  TC wacc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) wacc[k] = (TC)0;
+
+  // zero the FP64 Y entries this thread owns (only this thread ever touches them)
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int it = tid + k * NT;
+    if (it < n_items) {
+      const int i = it / nJB, jb = it - (it / nJB) * nJB;
+#pragma unroll
+      for (int c = 0; c < JB; ++c) {
+        const int j = jb * JB + c;
+        if (j < r) part[r + i + size_t(n) * j] = 0.0;
+      }
+    }
+  }
+
+  const int64_t num_tiles = (prm.p + TS - 1) / TS;
+  int since_flush = 0;
+  for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+    const int64_t s0 = tile * TS;
+    const int valid = (int)(prm.p - s0 < TS ? prm.p - s0 : TS);
+    __syncthreads();  // the previous tile's phase 2 is done with Vs and Ws
+    for (int e = tid; e < TS * n; e += NT) {
+      const int s = e / n, i = e - s * n;
+      TC v = (TC)0;
+      if (s < valid) {
+        v = widen<TC>(V[(s0 + s) * ld + i]);
+        if (DT == STMF_E4M3) v *= (TC)prm.scale[s0 + s];
+      }
+      Vs[s * vst + i] = v;
+    }
+    if (tid < TS)
+      nus[tid] = tid < valid ? (TC)(prm.nu ? prm.nu[s0 + tid] : prm.nu_uniform) : (TC)0;
+    __syncthreads();
+
+    // phase 1: z = v_s^T a_j for the thread's sample s and column quads q0, q0+4, ...
+    {
+      const int s = tid % TS;
+      const int q0 = tid / TS;
+      const TC nu_s = nus[s];
+      const TC* vrow = Vs + s * vst;
+#pragma unroll
+      for (int kq = 0; kq < 4; ++kq) {
+        const int q = q0 + 4 * kq;
+        if (4 * q < rp) {
+          TC z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+          const TC* acol = As + 4 * q;
+          for (int i = 0; i < n; ++i) {
+            const TC v = vrow[i];
+            const TC* a = acol + i * rp;
+            z0 += v * a[0];
+            z1 += v * a[1];
+            z2 += v * a[2];
+            z3 += v * a[3];
+          }
+          const TC zz[4] = {z0, z1, z2, z3};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const TC t = ipow(zz[c], d - 1);
+            Ws[s * rp + 4 * q + c] = nu_s * t;
+            wacc[kq * 4 + c] += nu_s * t * zz[c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // phase 2: Y[i][j] += sum_s V[s][i] W[s][j]
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int it = tid + k * NT;
+      if (it < n_items) {
+        const int i = it / nJB, jb = it - (it / nJB) * nJB;
+        const TC* wcol = Ws + jb * JB;
+        for (int s = 0; s < valid; ++s) {
+          const TC v = Vs[s * vst + i];
+          const TC* w = wcol + s * rp;
+#pragma unroll
+          for (int c = 0; c < JB; ++c) acc[k * JB + c] += v * w[c];
+        }
+      }
+    }
+
+    ++since_flush;
+    const bool last = tile + gridDim.x >= num_tiles;
+    if (since_flush == prm.flush_tiles || last) {
+      since_flush = 0;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const int it = tid + k * NT;
+        if (it < n_items) {
+          const int i = it / nJB, jb = it - (it / nJB) * nJB;
+#pragma unroll
+          for (int c = 0; c < JB; ++c) {
+            const int j = jb * JB + c;
+            if (j < r) part[r + i + size_t(n) * j] += (double)acc[k * JB + c];
+            acc[k * JB + c] = (TC)0;
+          }
+        }
+      }
+      // w: reduce over the warp's samples, then fold into the warp's FP64 row
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        double x = (double)wacc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wsh[warp * 16 + k] += x;
+        wacc[k] = (TC)0;
+      }
+    }
+  }
+  __syncthreads();
+  // w_j = sum over the two warps that own column quad q0 = (j/4) % 4, slot (j/4)/4
+  for (int j = tid; j < r; j += NT) {
+    const int q = j / 4, c = j % 4, q0 = q % 4, kq = q / 4;
+    part[j] = wsh[(2 * q0) * 16 + kq * 4 + c] + wsh[(2 * q0 + 1) * 16 + kq * 4 + c];
+  }
+}
+
+template <typename TC, int DT, int JB>
+cudaError_t launch_one(const FgParams& prm, int grid, cudaStream_t s) {
+  const size_t smem = smem_bytes<TC>(prm.n, prm.r_pad);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  fg_simt_kernel<TC, DT, JB><<<grid, NT, smem, s>>>(prm);
+  return cudaGetLastError();
+}
+
+template <typename TC, int DT>
+cudaError_t launch_jb(const FgParams& prm, int grid, cudaStream_t s) {
+  if (prm.r_pad % 16 == 0) return launch_one<TC, DT, 16>(prm, grid, s);
+  if (prm.r_pad % 8 == 0) return launch_one<TC, DT, 8>(prm, grid, s);
+  return launch_one<TC, DT, 4>(prm, grid, s);
+}
+
+}  // namespace
+
+size_t fg_simt_smem(int dtype, int n, int r) {
+  const int rp = (r + 3) / 4 * 4;
+  return dtype == STMF_F64 ? smem_bytes<double>(n, rp) : smem_bytes<float>(n, rp);
+}
+
+int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms) {
+  const int rp = (r + 3) / 4 * 4;
+  const size_t smem = dtype == STMF_F64 ? smem_bytes<double>(n, rp) : smem_bytes<float>(n, rp);
+  // blocks per SM bounded by shared memory (228 KB per SM) and registers (1 or 2 per SM)
+  int per_sm = (int)((228 * 1024) / (smem + 1024));
+  const int reg_cap = dtype == STMF_F64 ? 1 : 2;
+  per_sm = per_sm < 1 ? 1 : (per_sm > reg_cap ? reg_cap : per_sm);
+  const int64_t tiles = (p + TS - 1) / TS;
+  int64_t grid = int64_t(num_sms) * per_sm;
+  if (grid > tiles) grid = tiles;
+  return (int)(grid < 1 ? 1 : grid);
+}
+
+cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  switch (dtype) {
+    case STMF_F64: return launch_jb<double, STMF_F64>(prm, grid, s);
+    case STMF_F32: return launch_jb<float, STMF_F32>(prm, grid, s);
+    case STMF_BF16: return launch_jb<float, STMF_BF16>(prm, grid, s);
+    case STMF_E4M3: return launch_jb<float, STMF_E4M3>(prm, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace stmf

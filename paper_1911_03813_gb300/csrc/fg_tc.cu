@@ -1,0 +1,434 @@
+// Fused pass over BF16 samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM).
+//
+// Computes, per persistent CTA and over that CTA's sample tiles, the partial sums of Alg. 2
+// line 2 (Lemma 3.3, eq. Y) and of Lemma 3.5:
+//     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
+// reading every sample from HBM exactly once.
+//
+// Per 128-sample tile (V_t: 128 samples x n features, BF16, staged by TMA with the 128-byte
+// swizzle, one 16 KB region per 64 features):
+//   MMA1  Z  = V_t [A_hi | A_lo]           M = 128 samples, N = 2 RP, K = n     (TMEM)
+//   epi   z = Z_hi + Z_lo;  W = nu z^{d-1} (split into BF16 hi | lo);  w += nu z^d
+//   MMA2  Y += V_t^T [W_hi | W_lo]         M = 128 features (per block), N = 2 RP, K = 128
+// The same shared-memory tile is the K-major A operand of MMA1 and the MN-major A operand of
+// MMA2. A (FP64) is split once per CTA into BF16 hi/lo halves so that A_hi + A_lo carries ~16
+// significant bits; W is split the same way per tile. Both halves ride in one MMA along N, so
+// V is read from shared memory once per MMA.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA issuer,
+// warps 2-5 = epilogue (thread = TMEM lane = sample of the tile, or feature of the M-block).
+// Pipelines: S shared-memory stages of V; double-buffered Z (TMEM) and W (shared memory); Y
+// accumulates in TMEM and is folded into FP64 registers every `flush` tiles, with two TMEM
+// buffers so the MMAs never wait for the fold. Every wait is bounded: a wait that runs out sets
+// STMF_ETIMEOUT in the status word and all roles wind down, wait for their own copies and MMAs,
+// and free TMEM before the CTA exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "stmf_internal.h"
+#include "tc_common.cuh"
+
+namespace stmf {
+namespace {
+
+constexpr int TM = 128;                // samples per tile
+constexpr int REG_BYTES = TM * 128;    // one 64-feature region of a V tile (16 KB)
+constexpr int NTHREADS = 192;
+constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
+
+struct TcExtra {
+  int nload;      // regions loaded by TMA: ceil(n / 64)
+  int nreg;       // regions per stage, even: 2 * ceil(n / 128)
+  int stages;
+  int flush;      // tiles between folds of Y into FP64
+  int tmem_cols;
+  int smem_bytes;
+};
+
+template <int RP>
+struct Cfg {
+  static constexpr int N = 2 * RP;            // MMA N: [hi | lo]
+  static constexpr int W_REG = N * 128;       // one 64-sample region of W (N rows)
+  static constexpr int A_REG = N * 128;       // one 64-feature region of the A split
+};
+
+__device__ __forceinline__ float ipow_f(float z, int e) {
+  float t = z;
+  for (int k = 1; k < e; ++k) t *= z;
+  return t;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[N]) {
+  if constexpr (N == 32) {
+    tc::tmem_ld32(taddr, v);
+  } else {
+    static_assert(N == 16, "N must be 16 or 32");
+    tc::tmem_ld16(taddr, v);
+  }
+}
+
+template <int RP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
+  using C = Cfg<RP>;
+  constexpr int N = C::N;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = tc::smem_addr(smem_raw);
+  unsigned char* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+
+  const int S = ex.stages, nreg = ex.nreg, nload = ex.nload;
+  const int n = prm.n, r = prm.r, d = prm.d;
+  const uint32_t stage_bytes = uint32_t(nreg) * REG_BYTES;
+  unsigned char* sV = base;
+  unsigned char* sW = sV + size_t(S) * stage_bytes;
+  unsigned char* sA = sW + 2 * 2 * C::W_REG;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nreg) * C::A_REG);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* zfull = bars + 2 * S;
+  uint64_t* zempty = zfull + 2;
+  uint64_t* wfull = zempty + 2;
+  uint64_t* wempty = wfull + 2;
+  uint64_t* yfull = wempty + 2;
+  uint64_t* yempty = yfull + 2;
+  uint64_t* mma_done = yempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  double* wred = reinterpret_cast<double*>(mma_done + 2);  // 4 x RP
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&zfull[b], 1);
+      tc::mbar_init(&zempty[b], 128);
+      tc::mbar_init(&wfull[b], 128);
+      tc::mbar_init(&wempty[b], 1);
+      tc::mbar_init(&yfull[b], 1);
+      tc::mbar_init(&yempty[b], 128);
+    }
+    tc::mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
+
+  // A split: rows [0, RP) hold BF16(a_j), rows [RP, 2 RP) hold BF16(a_j - BF16(a_j)); K = feature.
+  {
+    const int kext = nreg * 64;
+    for (int e = tid; e < N * kext; e += NTHREADS) {
+      const int row = e / kext, k = e - row * kext;
+      const int j = row % RP;
+      double a = (j < r && k < n) ? prm.A[k + size_t(n) * j] : 0.0;
+      const __nv_bfloat16 hi = __double2bfloat16(a);
+      const __nv_bfloat16 v = row < RP ? hi : __double2bfloat16(a - (double)__bfloat162float(hi));
+      *reinterpret_cast<__nv_bfloat16*>(sA + (k >> 6) * C::A_REG + tc::sw128_offset(row, k & 63)) = v;
+    }
+    // regions of each V stage that TMA never loads (features beyond the last 64-block) are zero
+    const int zero_regs = nreg - nload;
+    if (zero_regs > 0) {
+      const int words = zero_regs * REG_BYTES / 16;
+      for (int s = 0; s < S; ++s) {
+        uint4* z = reinterpret_cast<uint4*>(sV + size_t(s) * stage_bytes + size_t(nload) * REG_BYTES);
+        for (int e = tid; e < words; e += NTHREADS) z[e] = make_uint4(0, 0, 0, 0);
+      }
+    }
+  }
+  tc::fence_proxy_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t num_tiles = (prm.p + TM - 1) / TM;
+  const int my_tiles = (int)((num_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int nmb = nreg / 2;
+  const int flush = ex.flush;
+  volatile int* abortv = abort_flag;
+  int no_abort = 0;
+  auto fail = [&]() {
+    stmf_set_status(prm.status, STMF_ETIMEOUT);
+    *abortv = 1;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < my_tiles; ++it) {
+        const int st = it % S;
+        const uint32_t ph = (it / S) & 1;
+        if (!tc::mbar_wait(&empty[st], ph ^ 1, abortv, WAIT_LIMIT)) {
+          fail();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&full[st], uint32_t(nload) * REG_BYTES);
+        const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
+        for (int g = 0; g < nload; ++g)
+          tc::tma_load_2d(sV + size_t(st) * stage_bytes + size_t(g) * REG_BYTES, &tmap, g * 64,
+                          (int32_t)(tile * TM), &full[st]);
+        ++issued;
+      }
+      // wait for the last copy issued into each stage (already complete unless we aborted)
+      for (int k = issued > S ? issued - S : 0; k < issued; ++k)
+        tc::mbar_wait(&full[k % S], (k / S) & 1, &no_abort, WAIT_LIMIT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc1 = tc::idesc_bf16(128, N, 0, 0);  // V K-major, A split K-major
+      const uint32_t idesc2 = tc::idesc_bf16(128, N, 1, 0);  // V^T MN-major, W K-major
+      const int k1 = (n + 15) / 16;
+      const uint32_t sv0 = tc::smem_addr(sV), sa0 = tc::smem_addr(sA), sw0 = tc::smem_addr(sW);
+      bool ok = true;
+      for (int it = 0; it <= my_tiles && ok; ++it) {
+        if (it < my_tiles) {
+          const int st = it % S, zb = it & 1;
+          ok = tc::mbar_wait(&full[st], (it / S) & 1, abortv, WAIT_LIMIT) &&
+               tc::mbar_wait(&zempty[zb], ((it >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
+          if (!ok) break;
+          tc::tc_fence_after();
+          const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
+          for (int kk = 0; kk < k1; ++kk) {
+            const uint64_t ad = tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
+            const uint64_t bd = tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
+            tc::mma_bf16(tmem + zb * N, ad, bd, idesc1, kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&zfull[zb]);
+        }
+        if (it > 0) {
+          const int t = it - 1;
+          const int st = t % S, wb = t & 1;
+          const int period = t / flush, yb = period & 1;
+          const bool first = (t % flush) == 0;
+          if (first) ok = tc::mbar_wait(&yempty[yb], ((period >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
+          ok = ok && tc::mbar_wait(&wfull[wb], (t >> 1) & 1, abortv, WAIT_LIMIT);
+          if (!ok) break;
+          tc::tc_fence_after();
+          const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
+          const uint32_t wbb = sw0 + uint32_t(wb) * 2 * C::W_REG;
+          for (int mb = 0; mb < nmb; ++mb) {
+            const uint32_t dY = tmem + 2 * N + uint32_t(yb * 2 + mb) * N;
+            for (int kk = 0; kk < TM / 16; ++kk) {
+              const uint64_t ad = tc::sdesc_sw128(vb + uint32_t(2 * mb) * REG_BYTES + kk * 2048,
+                                                  REG_BYTES, 1024);
+              const uint64_t bd = tc::sdesc_sw128(wbb + (kk >> 2) * C::W_REG + (kk & 3) * 32, 16, 1024);
+              tc::mma_bf16(dY, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
+            }
+          }
+          tc::mma_commit(&empty[st]);
+          tc::mma_commit(&wempty[wb]);
+          if ((t % flush) == flush - 1 || t == my_tiles - 1) tc::mma_commit(&yfull[yb]);
+        }
+      }
+      if (!ok) fail();
+      tc::mma_commit(mma_done);
+      tc::mbar_wait(mma_done, 0, &no_abort, WAIT_LIMIT);
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue (128 threads)
+    const int q = warp & 3;            // TMEM lane quarter this warp may access
+    const int L = 32 * q + lane;       // sample within the tile / feature within the M-block
+    const uint32_t lane_off = uint32_t(32 * q) << 16;
+    float wacc[RP];
+    double wacc_d[RP];
+    double yacc[2][RP];
+#pragma unroll
+    for (int j = 0; j < RP; ++j) {
+      wacc[j] = 0.f;
+      wacc_d[j] = 0.0;
+      yacc[0][j] = 0.0;
+      yacc[1][j] = 0.0;
+    }
+    bool ok = true;
+    for (int it = 0; it < my_tiles; ++it) {
+      const int zb = it & 1, wb = it & 1;
+      const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
+      const int64_t sidx = tile * TM + L;
+      float nu_s = 0.f;
+      if (sidx < prm.p) nu_s = prm.nu ? (float)prm.nu[sidx] : (float)prm.nu_uniform;
+      if (!tc::mbar_wait(&zfull[zb], (it >> 1) & 1, abortv, WAIT_LIMIT)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      float z[N];
+      tmem_load_row<N>(tmem + zb * N + lane_off, z);
+      tc::tmem_ld_wait();
+      tc::tc_fence_before();
+      tc::mbar_arrive(&zempty[zb]);
+      float wv[RP];
+#pragma unroll
+      for (int j = 0; j < RP; ++j) {
+        const float zz = z[j] + z[RP + j];
+        const float t = ipow_f(zz, d - 1);
+        wv[j] = nu_s * t;
+        wacc[j] += wv[j] * zz;
+      }
+      if (!tc::mbar_wait(&wempty[wb], ((it >> 1) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+        ok = false;
+        break;
+      }
+      unsigned char* wbuf = sW + size_t(wb) * 2 * C::W_REG + size_t(L >> 6) * C::W_REG;
+#pragma unroll
+      for (int j = 0; j < RP; ++j) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(wv[j]);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(wv[j] - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(j, L & 63)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(RP + j, L & 63)) = lo;
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&wfull[wb]);
+      if ((it % flush) == flush - 1 || it == my_tiles - 1) {
+        const int period = it / flush, yb = period & 1;
+        if (!tc::mbar_wait(&yfull[yb], (period >> 1) & 1, abortv, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+          if (mb < nmb) {
+            float y[N];
+            tmem_load_row<N>(tmem + 2 * N + uint32_t(yb * 2 + mb) * N + lane_off, y);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < RP; ++j) yacc[mb][j] += (double)y[j] + (double)y[RP + j];
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&yempty[yb]);
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+          wacc_d[j] += (double)wacc[j];
+          wacc[j] = 0.f;
+        }
+      }
+    }
+    if (!ok) {
+      fail();
+    } else {
+      double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+#pragma unroll
+      for (int mb = 0; mb < 2; ++mb) {
+        const int i = 128 * mb + L;
+        if (mb < nmb && i < n) {
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+            if (j < r) part[r + i + size_t(n) * j] = yacc[mb][j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RP; ++j) {
+        double x = wacc_d[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wred[q * RP + j] = x;
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (tid < r && !*abortv) {
+    double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+    part[tid] = wred[0 * RP + tid] + wred[1 * RP + tid] + wred[2 * RP + tid] + wred[3 * RP + tid];
+  }
+  if (warp == 1) tc::tmem_dealloc(tmem, ex.tmem_cols);
+}
+
+// ---------------------------------------------------------------------------------- host side
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+int rp_of(int r) { return r <= 8 ? 8 : 16; }
+
+TcExtra plan(int n, int r) {
+  TcExtra ex{};
+  ex.nload = (n + 63) / 64;
+  ex.nreg = 2 * ((n + 127) / 128);
+  const int RP = rp_of(r), N = 2 * RP;
+  const int fixed = 2 * 2 * N * 128 + ex.nreg * N * 128 + 1024 /*align*/ + 1024 /*barriers, w*/;
+  const int stage = ex.nreg * REG_BYTES;
+  int S = (232448 - fixed) / stage;
+  if (S > 8) S = 8;
+  ex.stages = S;
+  ex.flush = 32;
+  int cols = 6 * N;
+  int pow2 = 32;
+  while (pow2 < cols) pow2 <<= 1;
+  ex.tmem_cols = pow2;
+  ex.smem_bytes = fixed + S * stage;
+  return ex;
+}
+
+template <int RP>
+cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtra& ex, int grid,
+                      cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fg_tc_kernel<RP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  fg_tc_kernel<RP><<<grid, NTHREADS, ex.smem_bytes, s>>>(tmap, prm, ex);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t fg_tc_supported(int dtype, int n, int r) {
+  if (dtype != STMF_BF16) return 0;
+  if (r < 1 || r > 16 || n < 1 || n > 256) return 0;
+  if (!get_encode()) return 0;
+  const TcExtra ex = plan(n, r);
+  return ex.stages >= 2 ? 1 : 0;
+}
+
+int fg_tc_grid(int, int, int, int64_t p, int num_sms) {
+  const int64_t tiles = (p + TM - 1) / TM;
+  return (int)(tiles < num_sms ? tiles : num_sms);
+}
+
+cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  if (dtype != STMF_BF16) return cudaErrorNotSupported;
+  if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
+  EncodeFn enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
+  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * 2};
+  const cuuint32_t box[2] = {64, TM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(prm.V), dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const TcExtra ex = plan(prm.n, prm.r);
+  if (rp_of(prm.r) == 8) return launch_rp<8>(tmap, prm, ex, grid, s);
+  return launch_rp<16>(tmap, prm, ex, grid, s);
+}
+
+}  // namespace stmf

@@ -1,0 +1,300 @@
+// Host side of the C ABI declared in include/stmf.h: contexts, argument validation, workspace
+// management and the launch sequence of each entry point.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "stmf_internal.h"
+
+struct stmf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  void* ws = nullptr;        // device workspace (partials, reduced Y/w)
+  size_t ws_bytes = 0;
+  int32_t* status = nullptr; // device status word
+  std::string last_error;
+  bool profiling = false;    // record events around each fused pass
+  std::vector<cudaEvent_t> ev_pool;  // recorded pairs: [2k] start, [2k+1] end
+  size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr size_t kMaxSmem = 232448;  // dynamic shared memory per block on sm_103
+
+stmf_status fail(stmf_ctx* c, stmf_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+stmf_status cuda_fail(stmf_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, STMF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+stmf_status check_samples(stmf_ctx* c, const stmf_samples* V) {
+  if (!V) return fail(c, STMF_EINVAL, "V is NULL");
+  if (!V->data) return fail(c, STMF_EINVAL, "V->data is NULL");
+  const int eb = stmf::elem_bytes(V->dtype);
+  if (eb == 0) return fail(c, STMF_EINVAL, "V->dtype is not a stmf_dtype");
+  if (V->n < 1 || V->n > 256) return fail(c, STMF_EINVAL, "V->n must be in [1, 256]");
+  if (V->p < 1) return fail(c, STMF_EINVAL, "V->p must be >= 1");
+  if (V->p > (int64_t(1) << 40)) return fail(c, STMF_EINVAL, "V->p is too large");
+  if (V->ld < V->n) return fail(c, STMF_EINVAL, "V->ld must be >= V->n");
+  if ((V->ld * eb) % 16 != 0) return fail(c, STMF_EINVAL, "V->ld * element size must be a multiple of 16 bytes");
+  if ((reinterpret_cast<uintptr_t>(V->data) & 15) != 0) return fail(c, STMF_EINVAL, "V->data must be 16-byte aligned");
+  if (V->dtype == STMF_E4M3 && !V->scale) return fail(c, STMF_EINVAL, "E4M3 samples need V->scale");
+  if (V->dtype != STMF_E4M3 && V->scale) return fail(c, STMF_EINVAL, "V->scale is only used with E4M3 samples");
+  return STMF_OK;
+}
+
+stmf_status ensure_ws(stmf_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return STMF_OK;
+  size_t want = bytes + bytes / 4 + 4096;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize (workspace growth)");
+  if (c->ws) cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  e = cudaMalloc(&c->ws, want);
+  if (e != cudaSuccess) return fail(c, STMF_ENOMEM, "cudaMalloc of the workspace failed");
+  c->ws_bytes = want;
+  return STMF_OK;
+}
+
+struct FgPlan {
+  bool tc = false;
+  int grid = 0;
+  size_t partial_doubles = 0;  // grid * L
+  size_t L = 0;
+};
+
+FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
+  FgPlan pl;
+  const int n = (int)V->n;
+  pl.tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
+  pl.grid = pl.tc ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, c->num_sms)
+                  : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
+  pl.L = size_t(r) + size_t(n) * size_t(r);
+  pl.partial_doubles = size_t(pl.grid) * pl.L;
+  return pl;
+}
+
+size_t fg_ws_bytes(const FgPlan& pl) { return (pl.partial_doubles + pl.L) * sizeof(double); }
+
+size_t gram_ws_bytes(int grid) { return size_t(grid) * sizeof(double); }
+
+}  // namespace
+
+extern "C" {
+
+int stmf_version(void) { return 100; }
+
+const char* stmf_status_string(int s) {
+  switch (s) {
+    case STMF_OK: return "STMF_OK";
+    case STMF_EINVAL: return "STMF_EINVAL";
+    case STMF_ENOMEM: return "STMF_ENOMEM";
+    case STMF_ECUDA: return "STMF_ECUDA";
+    case STMF_ETIMEOUT: return "STMF_ETIMEOUT";
+    case STMF_ENONFINITE: return "STMF_ENONFINITE";
+    case STMF_ENOTREADY: return "STMF_ENOTREADY";
+    case STMF_ECANCELLED: return "STMF_ECANCELLED";
+    case STMF_EBUSY: return "STMF_EBUSY";
+    case STMF_EUNSUPPORTED: return "STMF_EUNSUPPORTED";
+    default: return "unknown status";
+  }
+}
+
+stmf_status stmf_create(int device, stmf_ctx_t* out) {
+  if (!out) return STMF_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) return STMF_EINVAL;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return STMF_ECUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return STMF_EUNSUPPORTED;
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return STMF_ECUDA;
+  stmf_ctx* c = new stmf_ctx();
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  e = cudaMalloc(&c->status, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    delete c;
+    return STMF_ENOMEM;
+  }
+  cudaMemset(c->status, 0, sizeof(int32_t));
+  cudaDeviceSynchronize();
+  *out = c;
+  return STMF_OK;
+}
+
+stmf_status stmf_destroy(stmf_ctx_t c) {
+  if (!c) return STMF_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->ws) cudaFree(c->ws);
+  if (c->status) cudaFree(c->status);
+  for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+  delete c;
+  return STMF_OK;
+}
+
+const char* stmf_last_error(stmf_ctx_t c) { return c ? c->last_error.c_str() : "NULL context"; }
+
+stmf_status stmf_device_status(stmf_ctx_t c, stmf_stream_t stream, int32_t* out_host) {
+  if (!c || !out_host) return fail(c, STMF_EINVAL, "NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->status, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stmf_device_status");
+  *out_host = v;
+  return STMF_OK;
+}
+
+stmf_status stmf_reserve(stmf_ctx_t c, const stmf_samples* V, int64_t r) {
+  if (!c) return STMF_EINVAL;
+  stmf_status st = check_samples(c, V);
+  if (st != STMF_OK) return st;
+  if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
+  const FgPlan pl = plan_fg(c, V, r);
+  const int gg = stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);
+  size_t need = fg_ws_bytes(pl);
+  if (gram_ws_bytes(gg) > need) need = gram_ws_bytes(gg);
+  return ensure_ws(c, need);
+}
+
+stmf_status stmf_fg(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32_t d, int64_t r,
+                    const double* lambda, const double* A, const double* alpha, double* f,
+                    double* g_lambda, double* G_A, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  stmf_status st = check_samples(c, V);
+  if (st != STMF_OK) return st;
+  if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
+  if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
+  if (!lambda || !A || !f || !g_lambda || !G_A) return fail(c, STMF_EINVAL, "NULL model or output pointer");
+  const int n = (int)V->n;
+  const FgPlan pl = plan_fg(c, V, r);
+  if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
+    return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
+  st = ensure_ws(c, fg_ws_bytes(pl));
+  if (st != STMF_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* partials = static_cast<double*>(c->ws);
+  double* yw = partials + pl.partial_doubles;
+
+  stmf::FgParams prm{};
+  prm.V = V->data;
+  prm.scale = V->scale;
+  prm.nu = nu;
+  prm.nu_uniform = 1.0 / double(V->p);
+  prm.A = A;
+  prm.partials = partials;
+  prm.p = V->p;
+  prm.n = n;
+  prm.ld = (int)V->ld;
+  prm.d = d;
+  prm.r = (int)r;
+  prm.r_pad = (int)((r + 3) / 4 * 4);
+  prm.flush_tiles = 16;
+  prm.status = c->status;
+  cudaEvent_t ev_end = nullptr;
+  if (c->profiling && c->ev_used + 2 <= 2 * 65536) {
+    while (c->ev_pool.size() < c->ev_used + 2) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) break;
+      c->ev_pool.push_back(ev);
+    }
+    if (c->ev_pool.size() >= c->ev_used + 2) {
+      cudaEventRecord(c->ev_pool[c->ev_used], s);
+      ev_end = c->ev_pool[c->ev_used + 1];
+      c->ev_used += 2;
+    }
+  }
+  cudaError_t e = pl.tc ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
+                        : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
+  if (ev_end) cudaEventRecord(ev_end, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fused pass launch");
+
+  stmf::ModelParams mp{};
+  mp.partials = partials;
+  mp.grid = pl.grid;
+  mp.A = A;
+  mp.lambda = lambda;
+  mp.alpha = alpha;
+  mp.f = f;
+  mp.g_lambda = g_lambda;
+  mp.G_A = G_A;
+  mp.yw = yw;
+  mp.n = n;
+  mp.r = (int)r;
+  mp.d = d;
+  mp.status = c->status;
+  e = stmf::model_terms_launch(mp, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "model terms launch");
+  return STMF_OK;
+}
+
+stmf_status stmf_profile_enable(stmf_ctx_t c, int32_t enable) {
+  if (!c) return STMF_EINVAL;
+  c->profiling = enable != 0;
+  return STMF_OK;
+}
+
+stmf_status stmf_profile_read(stmf_ctx_t c, double* total_ms, int64_t* count) {
+  if (!c || !total_ms || !count) return fail(c, STMF_EINVAL, "NULL argument");
+  double tot = 0.0;
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    cudaError_t e = cudaEventSynchronize(c->ev_pool[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+    tot += ms;
+  }
+  *total_ms = tot;
+  *count = (int64_t)(c->ev_used / 2);
+  c->ev_used = 0;
+  return STMF_OK;
+}
+
+stmf_status stmf_norm_x(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32_t d,
+                        double* alpha_out, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  stmf_status st = check_samples(c, V);
+  if (st != STMF_OK) return st;
+  if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
+  if (!alpha_out) return fail(c, STMF_EINVAL, "alpha_out is NULL");
+  if (V->dtype == STMF_F64 && V->n > 200)
+    return fail(c, STMF_EINVAL, "FP64 samples: n must be <= 200 for the Gram pass");
+  const int grid = stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);
+  st = ensure_ws(c, gram_ws_bytes(grid));
+  if (st != STMF_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  stmf::GramParams gp{};
+  gp.V = V->data;
+  gp.scale = V->scale;
+  gp.nu = nu;
+  gp.nu_uniform = 1.0 / double(V->p);
+  gp.partials = static_cast<double*>(c->ws);
+  gp.p = V->p;
+  gp.n = (int)V->n;
+  gp.ld = (int)V->ld;
+  gp.d = d;
+  gp.status = c->status;
+  cudaError_t e = stmf::gram_simt_launch(V->dtype, gp, grid, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gram pass launch");
+  e = stmf::reduce_scalar_launch(gp.partials, grid, alpha_out, c->status, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Gram reduction launch");
+  return STMF_OK;
+}
+
+}  // extern "C"

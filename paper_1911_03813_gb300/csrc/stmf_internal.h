@@ -1,0 +1,85 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "stmf.h"
+
+namespace stmf {
+
+// Launch parameters of the fused pass over V (Alg. 2 line 2 plus the sum of line 3).
+struct FgParams {
+  const void* V;        // sample-major storage, p rows of ld elements
+  const float* scale;   // per-sample scales (e4m3) or nullptr
+  const double* nu;     // p weights or nullptr (uniform nu_uniform)
+  double nu_uniform;
+  const double* A;      // n x r column-major FP64
+  double* partials;     // [grid][r + n*r]: w partial then Y partial (column-major n x r)
+  int64_t p;
+  int n, ld, d, r;
+  int r_pad;            // r rounded up to a multiple of 4
+  int flush_tiles;      // FP32 accumulators are folded into FP64 every flush_tiles tiles
+  int32_t* status;      // device status word
+};
+
+// Finalisation of Alg. 2 lines 3-9 from the reduced (w, Y).
+struct ModelParams {
+  const double* partials;  // [grid][L] with L = r + n*r
+  int grid;
+  const double* A;
+  const double* lambda;
+  const double* alpha;     // device scalar or nullptr
+  double* f;
+  double* g_lambda;
+  double* G_A;
+  double* yw;              // reduced w and Y, L doubles (workspace)
+  int n, r, d;
+  int32_t* status;
+};
+
+struct GramParams {
+  const void* V;
+  const float* scale;
+  const double* nu;
+  double nu_uniform;
+  double* partials;  // [grid]
+  int64_t p;
+  int n, ld, d;
+  int32_t* status;
+};
+
+// Host launchers, one per translation unit. Each returns cudaSuccess or the launch error.
+// `grid_out` receives the grid size used (partials has grid_out slots).
+size_t fg_simt_smem(int dtype, int n, int r);  // dynamic shared memory of the pass
+int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms);
+cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
+int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
+cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s);
+int gram_simt_grid(int dtype, int n, int64_t p, int num_sms);
+cudaError_t gram_simt_launch(int dtype, const GramParams& prm, int grid, cudaStream_t s);
+cudaError_t reduce_scalar_launch(const double* partials, int count, double* out,
+                                 int32_t* status, cudaStream_t s);
+
+inline int elem_bytes(int dtype) {
+  switch (dtype) {
+    case STMF_F64: return 8;
+    case STMF_F32: return 4;
+    case STMF_BF16: return 2;
+    case STMF_E4M3: return 1;
+    default: return 0;
+  }
+}
+
+}  // namespace stmf
+
+// Record a device-side error in the status word: the first error wins.
+#ifdef __CUDACC__
+__device__ __forceinline__ void stmf_set_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+#endif

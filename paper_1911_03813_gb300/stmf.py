@@ -1,0 +1,249 @@
+"""Python binding of libstmf (include/stmf.h): argument marshalling only.
+
+Every step of the evaluation runs in the library's CUDA kernels; this module passes torch device
+pointers, sizes and the current CUDA stream across the C ABI and raises StmfError on a non-zero
+status. There is no other implementation behind these names: if libstmf.so is missing or fails
+to load, every call raises.
+"""
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+STMF_F64, STMF_F32, STMF_BF16, STMF_E4M3 = 0, 1, 2, 3
+_TORCH_DTYPE = {
+    torch.float64: STMF_F64,
+    torch.float32: STMF_F32,
+    torch.bfloat16: STMF_BF16,
+    torch.float8_e4m3fn: STMF_E4M3,
+}
+_NAME_DTYPE = {"f64": STMF_F64, "f32": STMF_F32, "bf16": STMF_BF16, "e4m3": STMF_E4M3}
+
+
+class StmfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status_string(status), msg))
+        self.status = status
+
+
+class Samples(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("p", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libstmf.so (built in-tree by _build.build()); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libstmf.so is not built: run paper_1911_03813_gb300._build.build() "
+                               "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        L.stmf_version.restype = ctypes.c_int
+        L.stmf_status_string.restype = ctypes.c_char_p
+        L.stmf_status_string.argtypes = [ctypes.c_int]
+        L.stmf_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+        L.stmf_destroy.argtypes = [vp]
+        L.stmf_last_error.restype = ctypes.c_char_p
+        L.stmf_last_error.argtypes = [vp]
+        L.stmf_reserve.argtypes = [vp, ctypes.POINTER(Samples), i64]
+        L.stmf_device_status.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.stmf_fg.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, i64, dp, dp, dp, dp, dp, dp,
+                              vp]
+        L.stmf_norm_x.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, dp, vp]
+        L.stmf_profile_enable.argtypes = [vp, i32]
+        L.stmf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i64)]
+        for name in ("stmf_create", "stmf_destroy", "stmf_reserve", "stmf_device_status",
+                     "stmf_fg", "stmf_norm_x", "stmf_profile_enable", "stmf_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _declare_extras(L)
+        _lib = L
+    return _lib
+
+
+_extra_declarers = []
+
+
+def _declare_extras(L):
+    for fn in _extra_declarers:
+        fn(L)
+
+
+def status_string(status):
+    try:
+        return lib().stmf_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover
+        return "status %d" % status
+
+
+class Context:
+    """An stmf context on one CUDA device (owns the library's workspace)."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = lib().stmf_create(self.device, ctypes.byref(h))
+        if st != 0:
+            raise StmfError(st, "stmf_create(%d) failed" % self.device)
+        self.handle = h
+
+    def check(self, st, what):
+        if st != 0:
+            msg = lib().stmf_last_error(self.handle)
+            raise StmfError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def device_status(self, stream=None):
+        out = ctypes.c_int32()
+        self.check(lib().stmf_device_status(self.handle, _stream(stream), ctypes.byref(out)),
+                   "stmf_device_status")
+        return out.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().stmf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts = {}
+
+
+def default_context(device=None):
+    if device is None:
+        device = torch.cuda.current_device()
+    ctx = _contexts.get(device)
+    if ctx is None:
+        ctx = Context(device)
+        _contexts[device] = ctx
+    return ctx
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_f64(t, shape, name):
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA float64 tensor" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
+def as_samples(V, n=None, scale=None):
+    """Build the stmf_samples descriptor of a p x ld CUDA tensor (row l = sample l) whose first n
+    columns hold the samples. V may also be a dict as returned by inputs.to_storage. Returns
+    (descriptor, keep-alive tuple)."""
+    if isinstance(V, dict):
+        n = V["n"]
+        scale = V.get("scale")
+        V = V["data"]
+    if V.dim() != 2 or not V.is_cuda:
+        raise ValueError("V must be a 2-D CUDA tensor (p x ld)")
+    if V.stride(1) != 1:
+        raise ValueError("V rows must be contiguous")
+    dt = _TORCH_DTYPE.get(V.dtype)
+    if dt is None:
+        raise ValueError("unsupported sample dtype %s" % V.dtype)
+    if n is None:
+        n = V.shape[1]
+    desc = Samples(V.data_ptr(), scale.data_ptr() if scale is not None else None, int(n),
+                   int(V.shape[0]), int(V.stride(0)), dt, 0)
+    return desc, (V, scale)
+
+
+def fg(V, nu, d, lam, A, alpha=None, out=None, stream=None, ctx=None):
+    """f, g_lambda, G_A of Alg. 2 (stmf_fg). lam: (r,) float64 CUDA; A: (n, r) float64 CUDA in
+    column-major order (pass A as a Fortran-ordered view, e.g. At.T for At of shape (r, n)).
+    nu: (p,) float64 CUDA or None (1/p). alpha: (1,) float64 CUDA or None (0).
+    Returns device tensors (f (1,), g_lambda (r,), G_A as an (n, r) column-major view)."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    n, p = desc.n, desc.p
+    r = lam.shape[0]
+    _check_f64(lam, (r,), "lambda")
+    if A.dtype != torch.float64 or not A.is_cuda or tuple(A.shape) != (n, r):
+        raise ValueError("A must be an (n, r) CUDA float64 tensor")
+    if not ((A.stride(0) == 1 or n == 1) and (A.stride(1) == n or r == 1)):
+        raise ValueError("A must be column-major (A.stride() == (1, n))")
+    if nu is not None:
+        _check_f64(nu, (p,), "nu")
+    if alpha is not None:
+        _check_f64(alpha, (1,), "alpha")
+    if out is None:
+        f = torch.empty(1, dtype=torch.float64, device=lam.device)
+        gl = torch.empty(r, dtype=torch.float64, device=lam.device)
+        GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
+    else:
+        f, gl, GA = out
+    st = lib().stmf_fg(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d), int(r), _ptr(lam),
+                       _ptr(A), _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _stream(stream))
+    ctx.check(st, "stmf_fg")
+    del keep
+    return f, gl, GA
+
+
+def norm_x(V, nu, d, out=None, stream=None, ctx=None):
+    """alpha = ||X||^2 = nu^T (V^T V)^d nu (stmf_norm_x). Returns a (1,) float64 CUDA tensor."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    if nu is not None:
+        _check_f64(nu, (desc.p,), "nu")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=torch.device("cuda", ctx.device))
+    st = lib().stmf_norm_x(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d), _ptr(out),
+                           _stream(stream))
+    ctx.check(st, "stmf_norm_x")
+    del keep
+    return out
+
+
+def reserve(V, r, ctx=None):
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    ctx.check(lib().stmf_reserve(ctx.handle, ctypes.byref(desc), int(r)), "stmf_reserve")
+
+
+def profile_enable(enable, ctx=None):
+    """Record CUDA events around each fused pass of stmf_fg (benchmark timing)."""
+    ctx = ctx or default_context()
+    ctx.check(lib().stmf_profile_enable(ctx.handle, 1 if enable else 0), "stmf_profile_enable")
+
+
+def profile_read(ctx=None):
+    """(total pass milliseconds, number of passes) since the last read."""
+    ctx = ctx or default_context()
+    tot = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    ctx.check(lib().stmf_profile_read(ctx.handle, ctypes.byref(tot), ctypes.byref(cnt)),
+              "stmf_profile_read")
+    return tot.value, cnt.value

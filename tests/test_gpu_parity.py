@@ -1,0 +1,167 @@
+"""GPU parity of the C ABI entry points against the FP64 oracle (run with -m gpu).
+
+Inputs come from the seeded generators; the oracle evaluates Alg. 2 in FP64 on exactly the
+values the GPU reads (BF16 codes widened, E4M3 codes times their scales). Tolerances:
+  FP64 samples   1e-12  (normwise relative for g_lambda and G_A; f relative to the
+                          cancellation scale S = alpha + |lambda^T u| + 2 |w^T lambda|)
+  FP32 samples   1e-5
+  BF16 / E4M3    4e-5   (tensor-core pass: A and W are split into BF16 hi/lo pairs, so the
+                          products carry ~2^-17 relative error before FP32 accumulation)
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import formats  # noqa: E402
+from paper_1911_03813_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 4e-5, "e4m3": 4e-5}
+
+
+@pytest.fixture(scope="module")
+def stmf():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_03813_gb300 import stmf as s
+    torch.cuda.set_device(0)
+    return s
+
+
+def decoded(st):
+    bits = inputs.storage_bits(st)
+    if st["dtype"] == "bf16":
+        return formats.decode_bf16(bits)
+    if st["dtype"] == "e4m3":
+        return formats.dequantize_e4m3(bits, st["scale"].cpu().numpy())
+    return np.asarray(bits, dtype=np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_fg(stmf, st, nu, lam, A, d, alpha=None):
+    dev = torch.device("cuda", 0)
+    lam_t = torch.tensor(lam, dtype=torch.float64, device=dev)
+    A_t = torch.tensor(np.ascontiguousarray(A.T), dtype=torch.float64, device=dev).T
+    nu_t = None if nu is None else torch.tensor(nu, dtype=torch.float64, device=dev)
+    al = None if alpha is None else torch.tensor([alpha], dtype=torch.float64, device=dev)
+    f, gl, GA = stmf.fg(st, nu_t, d, lam_t, A_t, alpha=al)
+    torch.cuda.synchronize()
+    assert stmf.default_context().device_status() == 0
+    return f.item(), gl.cpu().numpy(), GA.cpu().numpy()
+
+
+def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0):
+    Vd = decoded(st)
+    f_ref, gl_ref, GA_ref, parts = oracle.fg_implicit(nu, Vd.T, lam, A, d, alpha=alpha,
+                                                      return_parts=True)
+    f, gl, GA = run_fg(stmf, st, nu, lam, A, d, alpha=alpha)
+    S = abs(alpha) + abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
+    assert abs(f - f_ref) <= tol * S, (f, f_ref, S)
+    assert rel(gl, gl_ref) <= tol, rel(gl, gl_ref)
+    assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
+    return f, gl, GA
+
+
+SHAPES = [
+    # n, p, r, d : tiles of 64/128 samples with ragged tails, r not a multiple of 4 or 16
+    (10, 1000, 2, 3),     # the small FP64 configuration's shape
+    (7, 1, 1, 3),         # a single sample
+    (1, 50, 3, 3),        # one feature
+    (33, 130, 5, 4),
+    (64, 5000, 8, 3),
+    (100, 20000, 10, 3),
+    (100, 20000, 10, 4),
+    (256, 70000, 16, 4),
+    (128, 3000, 64, 2),   # r at its maximum, the matrix case
+    (256, 300, 33, 5),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("n,p,r,d", SHAPES)
+def test_fg_parity(stmf, dtype, n, p, r, d):
+    if dtype == "f64" and n * ((r + 3) // 4 * 4) > 8192:
+        pytest.skip("FP64 path limited by shared memory at this n * r")
+    data = inputs.gmm(n, p, min(r, 8), 0.1, seed=n + p + r + d)
+    lam, A = inputs.random_model(n, r, seed=3 * r + d)
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    check_fg(stmf, st, None, lam, A, d, TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_fg_nonuniform_weights_and_alpha(stmf, dtype):
+    n, p, r, d = 40, 3001, 6, 4
+    data = inputs.gmm(n, p, 4, 0.05, seed=9)
+    nu = inputs.positive_weights(p, seed=10)
+    lam, A = inputs.random_model(n, r, seed=11)
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    alpha = oracle.norm_x(nu, decoded(st).T, d)
+    check_fg(stmf, st, nu, lam, A, d, TOL[dtype], alpha=alpha)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("n,p,d", [(10, 1000, 3), (33, 130, 4), (100, 700, 3), (5, 1, 4),
+                                   (200, 257, 2)])
+def test_norm_x_parity(stmf, dtype, n, p, d):
+    data = inputs.gmm(n, p, 3, 0.1, seed=p + d)
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    ref = oracle.norm_x(None, decoded(st).T, d)
+    got = stmf.norm_x(st, None, d).item()
+    assert abs(got - ref) <= max(TOL[dtype], 1e-6 if dtype != "f64" else 0) * abs(ref)
+
+
+def test_zero_residual_on_gpu(stmf):
+    """A = V, lambda = nu gives M = X: f = 0 and zero gradient (eq. tensorX)."""
+    n, p, d = 12, 9, 3
+    g = np.random.default_rng(4)
+    V = g.standard_normal((p, n))
+    nu = inputs.positive_weights(p, seed=5)
+    st = inputs.to_storage(V, "f64", device="cuda")
+    alpha = oracle.norm_x(nu, V.T, d)
+    f, gl, GA = run_fg(stmf, st, nu, nu, V.T.copy(), d, alpha=alpha)
+    assert abs(f) <= 1e-12 * alpha
+    assert np.abs(gl).max() <= 1e-12 * max(1.0, alpha)
+
+
+def test_permutation_of_components_on_gpu(stmf):
+    n, p, r, d = 50, 4000, 5, 4
+    data = inputs.gmm(n, p, 5, 0.1, seed=21)
+    lam, A = inputs.random_model(n, r, seed=22)
+    st = inputs.to_storage(data["V"], "f32", device="cuda")
+    f1, gl1, GA1 = run_fg(stmf, st, None, lam, A, d)
+    perm = np.array([3, 0, 4, 1, 2])
+    f2, gl2, GA2 = run_fg(stmf, st, None, lam[perm], A[:, perm], d)
+    assert abs(f1 - f2) <= 1e-6 * abs(f1)
+    assert rel(gl2, gl1[perm]) < 1e-5 and rel(GA2, GA1[:, perm]) < 1e-5
+
+
+def test_determinism(stmf):
+    n, p, r, d = 64, 50000, 8, 3
+    data = inputs.gmm(n, p, 8, 0.1, seed=31)
+    lam, A = inputs.random_model(n, r, seed=32)
+    for dtype in ("f32", "bf16"):
+        st = inputs.to_storage(data["V"], dtype, device="cuda")
+        a = run_fg(stmf, st, None, lam, A, d)
+        b = run_fg(stmf, st, None, lam, A, d)
+        assert a[0] == b[0]
+        assert np.array_equal(a[2], b[2])
+
+
+def test_invalid_arguments_raise(stmf):
+    st = inputs.to_storage(np.ones((10, 4)), "f32", device="cuda")
+    lam = torch.ones(2, dtype=torch.float64, device="cuda")
+    A = torch.ones((2, 4), dtype=torch.float64, device="cuda").T
+    with pytest.raises(stmf.StmfError):
+        stmf.fg(st, None, 9, lam, A)            # d out of range
+    with pytest.raises(stmf.StmfError):
+        stmf.fg(st, None, 1, lam, A)
+    big = torch.ones(65, dtype=torch.float64, device="cuda")
+    with pytest.raises((stmf.StmfError, ValueError)):
+        stmf.fg(st, None, 3, big, torch.ones((65, 4), dtype=torch.float64, device="cuda").T)
