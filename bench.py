@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=P_FULL)
+    ap.add_argument("--legs", default="bf16,fp32", help="sample types to time (bf16 is the headline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -208,17 +209,23 @@ def main():
             dist.barrier()
 
     P = args.p
-    st32 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="f32")
-    st16 = dict(st32)
-    st16["data"] = st32["data"].to(torch.bfloat16)
-    st16["dtype"] = "bf16"
-    st16["ld"] = inputs.padded_ld(N_FEAT, "bf16")
+    legs = args.legs.split(",")
+    if "fp32" in legs:
+        st32 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="f32")
+        st16 = dict(st32)
+        st16["data"] = st32["data"].to(torch.bfloat16)
+        st16["dtype"] = "bf16"
+        st16["ld"] = inputs.padded_ld(N_FEAT, "bf16")
+    else:
+        st16 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="bf16")
+        st32 = None
     lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
     lam_t = torch.tensor(lam, device=dev)
     A_t = torch.tensor(A.T.copy(), device=dev).T
     ctx = stmf.default_context(local)
     stmf.reserve(st16, R)
-    stmf.reserve(st32, R)
+    if st32 is not None:
+        stmf.reserve(st32, R)
     f = torch.empty(1, dtype=torch.float64, device=dev)
     gl = torch.empty(R, dtype=torch.float64, device=dev)
     GA = torch.empty((R, N_FEAT), dtype=torch.float64, device=dev).T
@@ -247,7 +254,10 @@ def main():
             pass_ms = tot / max(cnt, 1)
         return ms, pass_ms
 
-    ms32, pass32 = timed(st32, max(args.steps // 2, 1), args.warmup, prof=True)
+    if "fp32" in legs:
+        ms32, pass32 = timed(st32, max(args.steps // 2, 1), args.warmup, prof=True)
+    else:
+        ms32 = pass32 = float("nan")
     with ClockSampler(local) as clk:
         ms16, pass16 = timed(st16, args.steps, args.warmup, prof=True)
     if world > 1:
