@@ -152,6 +152,40 @@ stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu,
 stmf_status stmf_profile_enable(stmf_ctx_t ctx, int32_t enable);
 stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* count_host);
 
+/*
+ * stmf_fg_noalloc -- the evaluation of stmf_fg for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface variant of stmf_fg (same kernels, same
+ * arguments and results), added for callers such as code running inside a memory arena owned
+ * by another runtime that forbids outside allocations, or a launch path where an allocation
+ * would synchronise the device at the wrong time. stmf_fg cannot serve them because its context
+ * allocates a status word and grows a workspace with cudaMalloc.
+ *
+ * No context: the scratch (per-block partial sums, reduced Y and w, a status word) is one fixed
+ * 8 MiB array of device globals in the library, held by every GPU that loads the library until
+ * the process exits. The call never calls cudaMalloc, cudaFree or any allocating routine. The
+ * first call on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ *
+ * Limits: as for stmf_fg (n <= 256, r <= 64, 2 <= d <= 8). The pass runs at most
+ * floor(2^20 / ((n + 1) r)) - 1 blocks so that every request within these limits fits the
+ * scratch (a request outside them returns STMF_EINVAL before any work; STMF_ENOMEM would mean
+ * the scratch cannot hold two blocks' partials, which no valid n, r reaches).
+ *
+ * All calls on a device share the array and leave their contents in it; each call overwrites
+ * every partial it reads and clears the status word it uses. Calls whose work overlaps on the
+ * GPU (other streams or host threads) race on the array: serialise them.
+ *
+ *  V, nu, d, r, lambda, A, alpha, f, g_lambda, G_A   as for stmf_fg (device pointers).
+ *  status   device, 1 int32 owned by the caller, or NULL. When given, device-side errors
+ *           (e.g. STMF_ENONFINITE) are written there (the caller clears it); when NULL they go
+ *           to a word inside the scratch that the call clears first.
+ * Enqueued on `stream`; asynchronous; the current device must be the device of all pointers.
+ */
+stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, int32_t d, int64_t r,
+                            const double* lambda, const double* A, const double* alpha,
+                            double* f, double* g_lambda, double* G_A, int32_t* status,
+                            stmf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -247,3 +247,39 @@ def profile_read(ctx=None):
     ctx.check(lib().stmf_profile_read(ctx.handle, ctypes.byref(tot), ctypes.byref(cnt)),
               "stmf_profile_read")
     return tot.value, cnt.value
+
+
+def _declare_noalloc(L):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.stmf_fg_noalloc.argtypes = [ctypes.POINTER(Samples), vp, i32, i64, vp, vp, vp, vp, vp, vp,
+                                  vp, vp]
+    L.stmf_fg_noalloc.restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_noalloc)
+
+
+def fg_noalloc(V, nu, d, lam, A, alpha=None, out=None, status=None, stream=None):
+    """stmf_fg_noalloc: the same evaluation as fg(), for callers that cannot allocate device
+    memory; the library uses a fixed scratch array in its device globals instead of a context
+    workspace. Calls on one device share that array, so calls that overlap on the GPU race.
+    Output tensors (f, g_lambda, G_A) may be passed in `out` so that the call itself allocates
+    nothing; `status` is an optional (1,) int32 CUDA tensor that receives device-side errors."""
+    desc, keep = as_samples(V)
+    n, r = desc.n, lam.shape[0]
+    _check_f64(lam, (r,), "lambda")
+    if A.dtype != torch.float64 or not A.is_cuda or tuple(A.shape) != (n, r):
+        raise ValueError("A must be an (n, r) CUDA float64 tensor")
+    if out is None:
+        f = torch.empty(1, dtype=torch.float64, device=lam.device)
+        gl = torch.empty(r, dtype=torch.float64, device=lam.device)
+        GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
+    else:
+        f, gl, GA = out
+    st = lib().stmf_fg_noalloc(ctypes.byref(desc), _ptr(nu), int(d), int(r), _ptr(lam), _ptr(A),
+                               _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _ptr(status),
+                               _stream(stream))
+    if st != 0:
+        raise StmfError(st, "stmf_fg_noalloc")
+    del keep
+    return f, gl, GA
