@@ -160,14 +160,14 @@ stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* co
  * would synchronise the device at the wrong time. stmf_fg cannot serve them because its context
  * allocates a status word and grows a workspace with cudaMalloc.
  *
- * No context: the scratch (per-block partial sums, reduced Y and w, a status word) is one fixed
+ * No context: the scratch (block partial sums, reduced Y and w, A^T A, a status word) is one fixed
  * 8 MiB array of device globals in the library, held by every GPU that loads the library until
  * the process exits. The call never calls cudaMalloc, cudaFree or any allocating routine. The
  * first call on a device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
  *
  * Limits: as for stmf_fg (n <= 256, r <= 64, 2 <= d <= 8). The pass runs at most
- * floor(2^20 / ((n + 1) r)) - 1 blocks so that every request within these limits fits the
+ * floor((2^20 - r^2) / ((n + 1) r)) - 1 blocks so that every request within these limits fits the
  * scratch (a request outside them returns STMF_EINVAL before any work; STMF_ENOMEM would mean
  * the scratch cannot hold two blocks' partials, which no valid n, r reaches).
  *

@@ -6,9 +6,9 @@
 // hooks must not be re-entered, or a launch path where an allocation would synchronise the
 // device at the wrong moment. stmf_fg needs a context, and a context allocates its status word
 // and grows its workspace with cudaMalloc. This entry point needs neither: its scratch (the
-// per-block partial sums, the reduced Y and w, and a status word) lives in one fixed array in
-// the library's device globals, which every GPU that loads the library holds until the process
-// exits.
+// per-block partial sums, the reduced Y and w, B = A^T A, and a status word) lives in one fixed
+// array in the library's device globals, which every GPU that loads the library holds until the
+// process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the device address of
 // the array with cudaGetSymbolAddress and caches it; make that first call before any stream
@@ -83,7 +83,7 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   // the partials of `grid` blocks plus the reduced (w, Y) must fit the fixed scratch; the pass is
   // persistent, so fewer blocks only means fewer tiles in flight
   const size_t L = size_t(r) + size_t(n) * size_t(r);
-  const size_t max_grid = kScratchDoubles / L;
+  const size_t max_grid = (kScratchDoubles - size_t(r) * size_t(r)) / L;
   if (max_grid < 2) return STMF_ENOMEM;  // (n + 1) * r too large for the scratch
   if (size_t(grid) > max_grid - 1) grid = int(max_grid - 1);
 
@@ -126,6 +126,7 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   mp.g_lambda = g_lambda;
   mp.G_A = G_A;
   mp.yw = scratch + size_t(grid) * L;
+  mp.bmat = mp.yw + L;
   mp.n = n;
   mp.r = (int)r;
   mp.d = d;

@@ -15,8 +15,9 @@
 // significant bits; W is split the same way per tile. Both halves ride in one MMA along N, so
 // V is read from shared memory once per MMA.
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA issuer,
-// warps 2-5 = epilogue (thread = TMEM lane = sample of the tile, or feature of the M-block).
+// Warp roles (608 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
+// warp 2 = MMA2 issuer, warps 3-18 = epilogue in four warpgroups that split the components
+// (thread = TMEM lane = sample of the tile, or feature of the M-block).
 // Pipelines: S shared-memory stages of V; double-buffered Z (TMEM) and W (shared memory); Y
 // accumulates in TMEM and is folded into FP64 registers every `flush` tiles, with two TMEM
 // buffers so the MMAs never wait for the fold. Every wait is bounded: a wait that runs out sets
@@ -33,7 +34,9 @@ namespace {
 
 constexpr int TM = 128;                // samples per tile
 constexpr int REG_BYTES = TM * 128;    // one 64-feature region of a V tile (16 KB)
-constexpr int NTHREADS = 192;
+constexpr int EG = 4;                  // epilogue warpgroups (components split among them)
+constexpr int NEPI = 128 * EG;         // epilogue threads
+constexpr int NTHREADS = 96 + NEPI;    // producer warp, MMA1 warp, MMA2 warp, epilogue
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
 struct TcExtra {
@@ -43,6 +46,7 @@ struct TcExtra {
   int flush;      // tiles between folds of Y into FP64
   int tmem_cols;
   int smem_bytes;
+  int prefetch;   // tiles ahead of the TMA ring whose boxes are prefetched into L2
 };
 
 template <int RP>
@@ -58,13 +62,13 @@ __device__ __forceinline__ float ipow_f(float z, int e) {
   return t;
 }
 
-template <int N>
-__device__ __forceinline__ void tmem_load_row(uint32_t taddr, float (&v)[N]) {
-  if constexpr (N == 32) {
-    tc::tmem_ld32(taddr, v);
+template <int C>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
+  if constexpr (C == 4) {
+    tc::tmem_ld4(taddr, v);
   } else {
-    static_assert(N == 16, "N must be 16 or 32");
-    tc::tmem_ld16(taddr, v);
+    static_assert(C == 2, "2 or 4 columns per load");
+    tc::tmem_ld2(taddr, v);
   }
 }
 
@@ -92,10 +96,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* wempty = wfull + 2;
   uint64_t* yfull = wempty + 2;
   uint64_t* yempty = yfull + 2;
-  uint64_t* mma_done = yempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  uint64_t* mma_done = yempty + 2;  // [0]: MMA1 issuer, [1]: MMA2 issuer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  double* wred = reinterpret_cast<double*>(mma_done + 2);  // 4 x RP
+  double* wred = reinterpret_cast<double*>(mma_done + 3);  // 4 x RP
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -106,13 +110,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&zfull[b], 1);
-      tc::mbar_init(&zempty[b], 128);
-      tc::mbar_init(&wfull[b], 128);
+      tc::mbar_init(&zempty[b], NEPI / 32);  // one elected arrival per epilogue warp
+      tc::mbar_init(&wfull[b], NEPI / 32);
       tc::mbar_init(&wempty[b], 1);
       tc::mbar_init(&yfull[b], 1);
-      tc::mbar_init(&yempty[b], 128);
+      tc::mbar_init(&yempty[b], NEPI / 32);
     }
-    tc::mbar_init(mma_done, 1);
+    tc::mbar_init(&mma_done[0], 1);
+    tc::mbar_init(&mma_done[1], 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -160,8 +165,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
+      // L2 prefetch runs `prefetch` tiles ahead of the shared-memory ring, so the HBM stream
+      // does not wait for stages that the MMA/epilogue chain still holds.
+      const int pf = ex.prefetch;
+      for (int it = 0; it < pf && it < my_tiles; ++it) {
+        const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
+        for (int g = 0; g < nload; ++g) tc::tma_prefetch_l2_2d(&tmap, g * 64, (int32_t)(tile * TM));
+      }
       int issued = 0;
       for (int it = 0; it < my_tiles; ++it) {
+        if (pf > 0 && it + pf < my_tiles) {
+          const int64_t tile = blockIdx.x + int64_t(it + pf) * gridDim.x;
+          for (int g = 0; g < nload; ++g)
+            tc::tma_prefetch_l2_2d(&tmap, g * 64, (int32_t)(tile * TM));
+        }
         const int st = it % S;
         const uint32_t ph = (it / S) & 1;
         if (!tc::mbar_wait(&empty[st], ph ^ 1, abortv, WAIT_LIMIT)) {
@@ -180,72 +197,90 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::mbar_wait(&full[k % S], (k / S) & 1, &no_abort, WAIT_LIMIT);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------------ MMA1 issuer
+    // Z(t) = V_t [A_hi | A_lo] as soon as tile t has landed and its Z buffer is free.
     if (lane == 0) {
       const uint32_t idesc1 = tc::idesc_bf16(128, N, 0, 0);  // V K-major, A split K-major
-      const uint32_t idesc2 = tc::idesc_bf16(128, N, 1, 0);  // V^T MN-major, W K-major
       const int k1 = (n + 15) / 16;
-      const uint32_t sv0 = tc::smem_addr(sV), sa0 = tc::smem_addr(sA), sw0 = tc::smem_addr(sW);
+      const uint32_t sv0 = tc::smem_addr(sV), sa0 = tc::smem_addr(sA);
       bool ok = true;
-      for (int it = 0; it <= my_tiles && ok; ++it) {
-        if (it < my_tiles) {
-          const int st = it % S, zb = it & 1;
-          ok = tc::mbar_wait(&full[st], (it / S) & 1, abortv, WAIT_LIMIT) &&
-               tc::mbar_wait(&zempty[zb], ((it >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
-          if (!ok) break;
-          tc::tc_fence_after();
-          const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
-          for (int kk = 0; kk < k1; ++kk) {
-            const uint64_t ad = tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
-            const uint64_t bd = tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
-            tc::mma_bf16(tmem + zb * N, ad, bd, idesc1, kk > 0 ? 1u : 0u);
-          }
-          tc::mma_commit(&zfull[zb]);
+      for (int t = 0; t < my_tiles; ++t) {
+        const int st = t % S, zb = t & 1;
+        ok = tc::mbar_wait(&full[st], (t / S) & 1, abortv, WAIT_LIMIT) &&
+             tc::mbar_wait(&zempty[zb], ((t >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
+        for (int kk = 0; kk < k1; ++kk) {
+          const uint64_t ad = tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
+          const uint64_t bd =
+              tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
+          tc::mma_bf16(tmem + zb * N, ad, bd, idesc1, kk > 0 ? 1u : 0u);
         }
-        if (it > 0) {
-          const int t = it - 1;
-          const int st = t % S, wb = t & 1;
-          const int period = t / flush, yb = period & 1;
-          const bool first = (t % flush) == 0;
-          if (first) ok = tc::mbar_wait(&yempty[yb], ((period >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
-          ok = ok && tc::mbar_wait(&wfull[wb], (t >> 1) & 1, abortv, WAIT_LIMIT);
-          if (!ok) break;
-          tc::tc_fence_after();
-          const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
-          const uint32_t wbb = sw0 + uint32_t(wb) * 2 * C::W_REG;
-          for (int mb = 0; mb < nmb; ++mb) {
-            const uint32_t dY = tmem + 2 * N + uint32_t(yb * 2 + mb) * N;
-            for (int kk = 0; kk < TM / 16; ++kk) {
-              const uint64_t ad = tc::sdesc_sw128(vb + uint32_t(2 * mb) * REG_BYTES + kk * 2048,
-                                                  REG_BYTES, 1024);
-              const uint64_t bd = tc::sdesc_sw128(wbb + (kk >> 2) * C::W_REG + (kk & 3) * 32, 16, 1024);
-              tc::mma_bf16(dY, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
-            }
-          }
-          tc::mma_commit(&empty[st]);
-          tc::mma_commit(&wempty[wb]);
-          if ((t % flush) == flush - 1 || t == my_tiles - 1) tc::mma_commit(&yfull[yb]);
-        }
+        tc::mma_commit(&zfull[zb]);
       }
       if (!ok) fail();
-      tc::mma_commit(mma_done);
-      tc::mbar_wait(mma_done, 0, &no_abort, WAIT_LIMIT);
+      tc::mma_commit(&mma_done[0]);
+      tc::mbar_wait(&mma_done[0], 0, &no_abort, WAIT_LIMIT);
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------------ MMA2 issuer
+    // Y += V_t^T [W_hi | W_lo] as soon as W(t) is written; its completion frees the V stage.
+    // A separate issuing thread keeps this from queueing behind the next tile's MMA1 issue.
+    if (lane == 0) {
+      const uint32_t idesc2 = tc::idesc_bf16(128, N, 1, 0);  // V^T MN-major, W K-major
+      const uint32_t sv0 = tc::smem_addr(sV), sw0 = tc::smem_addr(sW);
+      bool ok = true;
+      for (int t = 0; t < my_tiles; ++t) {
+        const int st = t % S, wb = t & 1;
+        const int period = t / flush, yb = period & 1;
+        const bool first = (t % flush) == 0;
+        if (first) ok = tc::mbar_wait(&yempty[yb], ((period >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
+        ok = ok && tc::mbar_wait(&wfull[wb], (t >> 1) & 1, abortv, WAIT_LIMIT);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
+        const uint32_t wbb = sw0 + uint32_t(wb) * 2 * C::W_REG;
+        for (int mb = 0; mb < nmb; ++mb) {
+          const uint32_t dY = tmem + 2 * N + uint32_t(yb * 2 + mb) * N;
+          for (int kk = 0; kk < TM / 16; ++kk) {
+            const uint64_t ad = tc::sdesc_sw128(vb + uint32_t(2 * mb) * REG_BYTES + kk * 2048,
+                                                REG_BYTES, 1024);
+            const uint64_t bd =
+                tc::sdesc_sw128(wbb + (kk >> 2) * C::W_REG + (kk & 3) * 32, 16, 1024);
+            tc::mma_bf16(dY, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
+          }
+        }
+        tc::mma_commit(&empty[st]);
+        tc::mma_commit(&wempty[wb]);
+        if ((t % flush) == flush - 1 || t == my_tiles - 1) tc::mma_commit(&yfull[yb]);
+      }
+      if (!ok) fail();
+      tc::mma_commit(&mma_done[1]);
+      tc::mbar_wait(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
     }
   } else {
-    // ------------------------------------------------------------------ epilogue (128 threads)
+    // ------------------------------------------------------------------ epilogue
+    // EG warpgroups; warpgroup g owns components [g*CPG, (g+1)*CPG) of every sample of the tile
+    // (thread = TMEM lane = sample), so the per-tile work of one thread is CPG components.
+    constexpr int CPG = RP / EG;
+    const int g = (warp - 3) >> 2;
     const int q = warp & 3;            // TMEM lane quarter this warp may access
     const int L = 32 * q + lane;       // sample within the tile / feature within the M-block
+    const int j0 = g * CPG;
     const uint32_t lane_off = uint32_t(32 * q) << 16;
-    float wacc[RP];
-    double wacc_d[RP];
-    double yacc[2][RP];
+    float wacc[CPG];
+    double wacc_d[CPG];
+    double yacc[2][CPG];
 #pragma unroll
-    for (int j = 0; j < RP; ++j) {
-      wacc[j] = 0.f;
-      wacc_d[j] = 0.0;
-      yacc[0][j] = 0.0;
-      yacc[1][j] = 0.0;
+    for (int c = 0; c < CPG; ++c) {
+      wacc[c] = 0.f;
+      wacc_d[c] = 0.0;
+      yacc[0][c] = 0.0;
+      yacc[1][c] = 0.0;
     }
+    // byte offsets of this thread's W entries (rows j and RP + j, column L) in a W buffer
+    const uint32_t wcol = uint32_t(L >> 6) * C::W_REG;
     bool ok = true;
     for (int it = 0; it < my_tiles; ++it) {
       const int zb = it & 1, wb = it & 1;
@@ -258,33 +293,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       tc::tc_fence_after();
-      float z[N];
-      tmem_load_row<N>(tmem + zb * N + lane_off, z);
+      float zh[CPG], zl[CPG];
+      tmem_load_cols<CPG>(tmem + zb * N + j0 + lane_off, zh);
+      tmem_load_cols<CPG>(tmem + zb * N + RP + j0 + lane_off, zl);
       tc::tmem_ld_wait();
       tc::tc_fence_before();
-      tc::mbar_arrive(&zempty[zb]);
-      float wv[RP];
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&zempty[zb]);
+      float wv[CPG];
 #pragma unroll
-      for (int j = 0; j < RP; ++j) {
-        const float zz = z[j] + z[RP + j];
+      for (int c = 0; c < CPG; ++c) {
+        const float zz = zh[c] + zl[c];
         const float t = ipow_f(zz, d - 1);
-        wv[j] = nu_s * t;
-        wacc[j] += wv[j] * zz;
+        wv[c] = nu_s * t;
+        wacc[c] += wv[c] * zz;
       }
       if (!tc::mbar_wait(&wempty[wb], ((it >> 1) & 1) ^ 1, abortv, WAIT_LIMIT)) {
         ok = false;
         break;
       }
-      unsigned char* wbuf = sW + size_t(wb) * 2 * C::W_REG + size_t(L >> 6) * C::W_REG;
+      unsigned char* wbuf = sW + size_t(wb) * 2 * C::W_REG + wcol;
 #pragma unroll
-      for (int j = 0; j < RP; ++j) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(wv[j]);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(wv[j] - __bfloat162float(hi));
+      for (int c = 0; c < CPG; ++c) {
+        const int j = j0 + c;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(wv[c]);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(wv[c] - __bfloat162float(hi));
         *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(j, L & 63)) = hi;
         *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(RP + j, L & 63)) = lo;
       }
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive(&wfull[wb]);
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&wfull[wb]);
       if ((it % flush) == flush - 1 || it == my_tiles - 1) {
         const int period = it / flush, yb = period & 1;
         if (!tc::mbar_wait(&yfull[yb], (period >> 1) & 1, abortv, WAIT_LIMIT)) {
@@ -295,19 +334,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int mb = 0; mb < 2; ++mb) {
           if (mb < nmb) {
-            float y[N];
-            tmem_load_row<N>(tmem + 2 * N + uint32_t(yb * 2 + mb) * N + lane_off, y);
+            float yh[CPG], yl[CPG];
+            const uint32_t ycol = tmem + 2 * N + uint32_t(yb * 2 + mb) * N + j0 + lane_off;
+            tmem_load_cols<CPG>(ycol, yh);
+            tmem_load_cols<CPG>(ycol + RP, yl);
             tc::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < RP; ++j) yacc[mb][j] += (double)y[j] + (double)y[RP + j];
+            for (int c = 0; c < CPG; ++c) yacc[mb][c] += (double)yh[c] + (double)yl[c];
           }
         }
         tc::tc_fence_before();
-        tc::mbar_arrive(&yempty[yb]);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&yempty[yb]);
 #pragma unroll
-        for (int j = 0; j < RP; ++j) {
-          wacc_d[j] += (double)wacc[j];
-          wacc[j] = 0.f;
+        for (int c = 0; c < CPG; ++c) {
+          wacc_d[c] += (double)wacc[c];
+          wacc[c] = 0.f;
         }
       }
     }
@@ -320,16 +362,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int i = 128 * mb + L;
         if (mb < nmb && i < n) {
 #pragma unroll
-          for (int j = 0; j < RP; ++j)
-            if (j < r) part[r + i + size_t(n) * j] = yacc[mb][j];
+          for (int c = 0; c < CPG; ++c)
+            if (j0 + c < r) part[r + i + size_t(n) * (j0 + c)] = yacc[mb][c];
         }
       }
 #pragma unroll
-      for (int j = 0; j < RP; ++j) {
-        double x = wacc_d[j];
+      for (int c = 0; c < CPG; ++c) {
+        double x = wacc_d[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) wred[q * RP + j] = x;
+        if (lane == 0) wred[q * RP + j0 + c] = x;
       }
     }
   }
@@ -380,6 +422,7 @@ TcExtra plan(int n, int r) {
   while (pow2 < cols) pow2 <<= 1;
   ex.tmem_cols = pow2;
   ex.smem_bytes = fixed + S * stage;
+  ex.prefetch = 4;
   return ex;
 }
 

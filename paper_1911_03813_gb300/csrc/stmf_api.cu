@@ -83,7 +83,9 @@ FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
   return pl;
 }
 
-size_t fg_ws_bytes(const FgPlan& pl) { return (pl.partial_doubles + pl.L) * sizeof(double); }
+size_t fg_ws_bytes(const FgPlan& pl, int64_t r) {
+  return (pl.partial_doubles + pl.L + size_t(r) * size_t(r)) * sizeof(double);
+}
 
 size_t gram_ws_bytes(int grid) { return size_t(grid) * sizeof(double); }
 
@@ -167,7 +169,7 @@ stmf_status stmf_reserve(stmf_ctx_t c, const stmf_samples* V, int64_t r) {
   if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
   const FgPlan pl = plan_fg(c, V, r);
   const int gg = stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);
-  size_t need = fg_ws_bytes(pl);
+  size_t need = fg_ws_bytes(pl, r);
   if (gram_ws_bytes(gg) > need) need = gram_ws_bytes(gg);
   return ensure_ws(c, need);
 }
@@ -185,7 +187,7 @@ stmf_status stmf_fg(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32
   const FgPlan pl = plan_fg(c, V, r);
   if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
     return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
-  st = ensure_ws(c, fg_ws_bytes(pl));
+  st = ensure_ws(c, fg_ws_bytes(pl, r));
   if (st != STMF_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* partials = static_cast<double*>(c->ws);
@@ -234,6 +236,7 @@ stmf_status stmf_fg(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32
   mp.g_lambda = g_lambda;
   mp.G_A = G_A;
   mp.yw = yw;
+  mp.bmat = yw + pl.L;
   mp.n = n;
   mp.r = (int)r;
   mp.d = d;

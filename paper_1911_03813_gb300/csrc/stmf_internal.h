@@ -36,6 +36,7 @@ struct ModelParams {
   double* g_lambda;
   double* G_A;
   double* yw;              // reduced w and Y, L doubles (workspace)
+  double* bmat;            // B = A^T A, r*r doubles (workspace)
   int n, r, d;
   int32_t* status;
 };
