@@ -19,8 +19,10 @@
 // warp 2 = MMA2 issuer, warps 3-18 = epilogue in four warpgroups that split the components
 // (thread = TMEM lane = sample of the tile, or feature of the M-block).
 // Pipelines: S shared-memory stages of V; double-buffered Z (TMEM) and W (shared memory); Y
-// accumulates in TMEM and is folded into FP64 registers every `flush` tiles, with two TMEM
-// buffers so the MMAs never wait for the fold. Every wait is bounded: a wait that runs out sets
+// accumulates in TMEM and is folded into compensated FP32 registers every `flush` tiles (FP64
+// from the block partials on), with two TMEM
+// buffers so the MMAs never wait for the fold and the epilogue folds whenever the buffer is
+// done rather than waiting for it. Every wait is bounded: a wait that runs out sets
 // STMF_ETIMEOUT in the status word and all roles wind down, wait for their own copies and MMAs,
 // and free TMEM before the CTA exits.
 #include <cuda.h>
@@ -46,7 +48,6 @@ struct TcExtra {
   int flush;      // tiles between folds of Y into FP64
   int tmem_cols;
   int smem_bytes;
-  int prefetch;   // tiles ahead of the TMA ring whose boxes are prefetched into L2
 };
 
 template <int RP>
@@ -55,6 +56,15 @@ struct Cfg {
   static constexpr int W_REG = N * 128;       // one 64-sample region of W (N rows)
   static constexpr int A_REG = N * 128;       // one 64-feature region of the A split
 };
+
+// Compensated FP32 accumulation (Kahan): s + c carries the running sum to about twice FP32's
+// precision without the FP64 pipe, which is a small fraction of FP32 throughput on this part.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 
 __device__ __forceinline__ float ipow_f(float z, int e) {
   float t = z;
@@ -165,20 +175,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      // L2 prefetch runs `prefetch` tiles ahead of the shared-memory ring, so the HBM stream
-      // does not wait for stages that the MMA/epilogue chain still holds.
-      const int pf = ex.prefetch;
-      for (int it = 0; it < pf && it < my_tiles; ++it) {
-        const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
-        for (int g = 0; g < nload; ++g) tc::tma_prefetch_l2_2d(&tmap, g * 64, (int32_t)(tile * TM));
-      }
       int issued = 0;
       for (int it = 0; it < my_tiles; ++it) {
-        if (pf > 0 && it + pf < my_tiles) {
-          const int64_t tile = blockIdx.x + int64_t(it + pf) * gridDim.x;
-          for (int g = 0; g < nload; ++g)
-            tc::tma_prefetch_l2_2d(&tmap, g * 64, (int32_t)(tile * TM));
-        }
         const int st = it % S;
         const uint32_t ph = (it / S) & 1;
         if (!tc::mbar_wait(&empty[st], ph ^ 1, abortv, WAIT_LIMIT)) {
@@ -269,18 +267,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int L = 32 * q + lane;       // sample within the tile / feature within the M-block
     const int j0 = g * CPG;
     const uint32_t lane_off = uint32_t(32 * q) << 16;
-    float wacc[CPG];
-    double wacc_d[CPG];
-    double yacc[2][CPG];
+    // per-period FP32 sums of w are folded with the Y periods into compensated FP32 totals
+    float wacc[CPG], ws[CPG], wc[CPG], ys[2][CPG], yc[2][CPG];
 #pragma unroll
     for (int c = 0; c < CPG; ++c) {
-      wacc[c] = 0.f;
-      wacc_d[c] = 0.0;
-      yacc[0][c] = 0.0;
-      yacc[1][c] = 0.0;
+      wacc[c] = ws[c] = wc[c] = 0.f;
+      ys[0][c] = yc[0][c] = ys[1][c] = yc[1][c] = 0.f;
     }
     // byte offsets of this thread's W entries (rows j and RP + j, column L) in a W buffer
     const uint32_t wcol = uint32_t(L >> 6) * C::W_REG;
+    int pending = -1;  // Y period whose fold is outstanding
+    // Fold period `per` if its MMAs are done (or wait for them when `force`); clears `pending`
+    // once folded. Returns false if a forced wait ran out.
+    auto fold = [&](int per, bool force) -> bool {
+      const int yb = per & 1;
+      const uint32_t par = (per >> 1) & 1;
+      if (!tc::mbar_test_wait(&yfull[yb], par)) {
+        if (!force) return true;
+        if (!tc::mbar_wait(&yfull[yb], par, abortv, WAIT_LIMIT)) return false;
+      }
+      tc::tc_fence_after();
+#pragma unroll
+      for (int mb = 0; mb < 2; ++mb) {
+        if (mb < nmb) {
+          float yh[CPG], yl[CPG];
+          const uint32_t ycol = tmem + 2 * N + uint32_t(yb * 2 + mb) * N + j0 + lane_off;
+          tmem_load_cols<CPG>(ycol, yh);
+          tmem_load_cols<CPG>(ycol + RP, yl);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < CPG; ++c) {
+            kahan_add(ys[mb][c], yc[mb][c], yh[c]);
+            kahan_add(ys[mb][c], yc[mb][c], yl[c]);
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&yempty[yb]);
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) {
+        kahan_add(ws[c], wc[c], wacc[c]);
+        wacc[c] = 0.f;
+      }
+      pending = -1;
+      return true;
+    };
     bool ok = true;
     for (int it = 0; it < my_tiles; ++it) {
       const int zb = it & 1, wb = it & 1;
@@ -324,32 +356,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&wfull[wb]);
-      if ((it % flush) == flush - 1 || it == my_tiles - 1) {
-        const int period = it / flush, yb = period & 1;
-        if (!tc::mbar_wait(&yfull[yb], (period >> 1) & 1, abortv, WAIT_LIMIT)) {
+      // Fold a finished Y period into FP64 once its MMAs have completed. The fold is polled on
+      // later tiles rather than waited for, so the epilogue never stalls behind MMA2; Y is
+      // double-buffered, so MMA2 needs this buffer back only a whole period later. A fold that
+      // is still outstanding is forced on the tile before the next period ends, at a period's
+      // end if one is somehow still pending, and on the CTA's last tile.
+      const bool period_end = (it % flush) == flush - 1 || it == my_tiles - 1;
+      if (period_end && pending >= 0 && !fold(pending, true)) {
+        ok = false;
+        break;
+      }
+      if (period_end) pending = it / flush;
+      if (pending >= 0) {
+        const bool force = it == my_tiles - 1 || (it % flush) == flush - 2;
+        if (!fold(pending, force)) {
           ok = false;
           break;
-        }
-        tc::tc_fence_after();
-#pragma unroll
-        for (int mb = 0; mb < 2; ++mb) {
-          if (mb < nmb) {
-            float yh[CPG], yl[CPG];
-            const uint32_t ycol = tmem + 2 * N + uint32_t(yb * 2 + mb) * N + j0 + lane_off;
-            tmem_load_cols<CPG>(ycol, yh);
-            tmem_load_cols<CPG>(ycol + RP, yl);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int c = 0; c < CPG; ++c) yacc[mb][c] += (double)yh[c] + (double)yl[c];
-          }
-        }
-        tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&yempty[yb]);
-#pragma unroll
-        for (int c = 0; c < CPG; ++c) {
-          wacc_d[c] += (double)wacc[c];
-          wacc[c] = 0.f;
         }
       }
     }
@@ -363,12 +385,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (mb < nmb && i < n) {
 #pragma unroll
           for (int c = 0; c < CPG; ++c)
-            if (j0 + c < r) part[r + i + size_t(n) * (j0 + c)] = yacc[mb][c];
+            if (j0 + c < r)
+              part[r + i + size_t(n) * (j0 + c)] = (double)ys[mb][c] - (double)yc[mb][c];
         }
       }
 #pragma unroll
       for (int c = 0; c < CPG; ++c) {
-        double x = wacc_d[c];
+        double x = (double)ws[c] - (double)wc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) wred[q * RP + j0 + c] = x;
@@ -416,13 +439,12 @@ TcExtra plan(int n, int r) {
   int S = (232448 - fixed) / stage;
   if (S > 8) S = 8;
   ex.stages = S;
-  ex.flush = 32;
+  ex.flush = 16;
   int cols = 6 * N;
   int pow2 = 32;
   while (pow2 < cols) pow2 <<= 1;
   ex.tmem_cols = pow2;
   ex.smem_bytes = fixed + S * stage;
-  ex.prefetch = 4;
   return ex;
 }
 

@@ -1,9 +1,8 @@
 // Model terms and outputs of Alg. 2 (lines 3-9), in FP64.
 //
-// reduce_kernel:   (w, Y) = sum over the pass's blocks of their FP64 partials (one thread per
-//                  entry; four interleaved running sums over the blocks, combined in a fixed
-//                  order, so results are reproducible bit for bit), and, in one extra block,
-//                  B = A^T A (Alg. 2 line 4).
+// reduce_kernel:   (w, Y) = sum over the pass's blocks of their FP64 partials (16 threads per
+//                  entry, combined in a fixed order, so results are reproducible bit for bit),
+//                  and, in extra blocks, B = A^T A (Alg. 2 line 4), one warp per entry.
 // finalize_kernel: C = B^{d-1} (line 5), then one thread per entry of
 //                  G_A = -2 d (Y - A D_lambda C) D_lambda (line 9, eq. gradb); block 0 also forms
 //                  u = (B * C) lambda (line 6, Lemma 3.4), f = alpha + lambda^T u - 2 w^T lambda
@@ -22,34 +21,53 @@ __device__ __forceinline__ double ipow_d(double z, int e) {
   return t;
 }
 
-__global__ void __launch_bounds__(RT) reduce_kernel(const ModelParams prm, int L, int nb) {
+// Block (RE x RY): thread (x, y) sums the partials of blocks y, y + RY, y + 2 RY, ... of entry
+// e = blockIdx.x * RE + x, issuing all of its loads before adding; the RY sums are then added in
+// y order. The order is fixed, so results are reproducible bit for bit.
+constexpr int RE = 32;    // entries per block
+constexpr int RY = 16;    // threads per entry
+constexpr int RMAX = 20;  // loads per thread (pass grid <= RY * RMAX = 320 blocks)
+
+__global__ void __launch_bounds__(RE * RY) reduce_kernel(const ModelParams prm, int L, int nb) {
+  __shared__ double red[RY][RE];
+  const int x = threadIdx.x % RE, y = threadIdx.x / RE;
   if ((int)blockIdx.x < nb) {
-    const int e = blockIdx.x * RT + threadIdx.x;
-    if (e >= L) return;
-    const double* p = prm.partials + e;
-    const size_t stride = size_t(L);
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int g = 0;
-    for (; g + 3 < prm.grid; g += 4) {
-      s0 += p[size_t(g) * stride];
-      s1 += p[size_t(g + 1) * stride];
-      s2 += p[size_t(g + 2) * stride];
-      s3 += p[size_t(g + 3) * stride];
+    const int e = blockIdx.x * RE + x;
+    double s = 0.0;
+    if (e < L) {
+      const double* p = prm.partials + e;
+      double v[RMAX];
+#pragma unroll
+      for (int k = 0; k < RMAX; ++k) {
+        const int g = y + k * RY;
+        v[k] = g < prm.grid ? p[size_t(g) * L] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < RMAX; ++k) s += v[k];
     }
-    for (; g < prm.grid; ++g) s0 += p[size_t(g) * stride];
-    prm.yw[e] = (s0 + s1) + (s2 + s3);
+    red[y][x] = s;
+    __syncthreads();
+    if (y == 0 && e < L) {
+      double t = red[0][x];
+#pragma unroll
+      for (int k = 1; k < RY; ++k) t += red[k][x];
+      prm.yw[e] = t;
+    }
     return;
   }
-  // B = A^T A (symmetric; each entry from its own dot product)
+  // B = A^T A: one warp per entry, lanes stride the features, then a fixed-order warp sum
   const int n = prm.n, r = prm.r;
-  for (int e = threadIdx.x; e < r * r; e += RT) {
-    const int j = e / r, k = e - j * r;
-    const double* aj = prm.A + size_t(n) * j;
-    const double* ak = prm.A + size_t(n) * k;
-    double b = 0.0;
-    for (int i = 0; i < n; ++i) b += aj[i] * ak[i];
-    prm.bmat[e] = b;
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = (blockIdx.x - nb) * (RE * RY / 32) + warp;
+  if (e >= r * r) return;
+  const int j = e / r, k = e - j * r;
+  const double* aj = prm.A + size_t(n) * j;
+  const double* ak = prm.A + size_t(n) * k;
+  double b = 0.0;
+  for (int i = lane; i < n; i += 32) b += aj[i] * ak[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+  if (lane == 0) prm.bmat[e] = b;
 }
 
 __global__ void __launch_bounds__(RT) finalize_kernel(const ModelParams prm) {
@@ -106,8 +124,10 @@ __global__ void reduce_scalar_kernel(const double* __restrict__ partials, int co
 
 cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s) {
   const int L = prm.r + prm.n * prm.r;
-  const int nb = (L + RT - 1) / RT;
-  reduce_kernel<<<nb + 1, RT, 0, s>>>(prm, L, nb);
+  const int nb = (L + RE - 1) / RE;
+  if (prm.grid > RY * RMAX) return cudaErrorInvalidValue;
+  const int nbB = (prm.r * prm.r + (RE * RY / 32) - 1) / (RE * RY / 32);
+  reduce_kernel<<<nb + nbB, RE * RY, 0, s>>>(prm, L, nb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   finalize_kernel<<<(prm.n * prm.r + RT - 1) / RT, RT, 0, s>>>(prm);

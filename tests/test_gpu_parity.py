@@ -165,3 +165,49 @@ def test_invalid_arguments_raise(stmf):
     big = torch.ones(65, dtype=torch.float64, device="cuda")
     with pytest.raises((stmf.StmfError, ValueError)):
         stmf.fg(st, None, 3, big, torch.ones((65, 4), dtype=torch.float64, device="cuda").T)
+
+
+def _oracle_on_device_storage(st, lam, A, d, nu=None, chunk=1 << 16):
+    """FP64 oracle over a device-resident sample block, decoded chunk by chunk on the host."""
+    data = st["data"]
+    p, n = data.shape[0], st["n"]
+
+    def cols(c0, c1):
+        blk = dict(st)
+        blk["data"] = data[c0:c1]
+        if st.get("scale") is not None:
+            blk["scale"] = st["scale"][c0:c1]
+        return decoded(blk).T
+
+    return oracle.fg_implicit(nu, cols, lam, A, d, p=p, chunk=chunk, return_parts=True)
+
+
+def test_fg_many_tiles_per_block(stmf):
+    """2^21 BF16 samples: every block of the tensor-core pass crosses several FP64 fold periods."""
+    n, p, r, d = 64, 1 << 21, 12, 3
+    st = inputs.gmm_device(n, p, 12, 0.1, seed=77, device="cuda", out_dtype="bf16")
+    lam, A = inputs.random_model(n, r, seed=78)
+    f_ref, gl_ref, GA_ref, parts = _oracle_on_device_storage(st, lam, A, d)
+    f, gl, GA = run_fg(stmf, st, None, lam, A, d)
+    S = abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
+    assert abs(f - f_ref) <= TOL["bf16"] * S
+    assert rel(gl, gl_ref) <= TOL["bf16"] and rel(GA, GA_ref) <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("dtype,n,p,r,d,sigma", [
+    ("bf16", 256, 1 << 24, 16, 4, 0.1),     # the benchmark's workload, full size
+    ("bf16", 256, 1 << 24, 16, 4, 1e-3),
+    ("f32", 100, 2500000, 10, 3, 0.1),      # the FP32 workload at scale, full size
+])
+def test_fg_full_size(stmf, dtype, n, p, r, d, sigma):
+    st = inputs.gmm_device(n, p, r, sigma, seed=2024, device="cuda", out_dtype=dtype)
+    lam, A = inputs.random_model(n, r, seed=2025)
+    f_ref, gl_ref, GA_ref, parts = _oracle_on_device_storage(st, lam, A, d)
+    f, gl, GA = run_fg(stmf, st, None, lam, A, d)
+    S = abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
+    tol = TOL[dtype]
+    assert abs(f - f_ref) <= tol * S, (f, f_ref, S)
+    assert rel(gl, gl_ref) <= tol, rel(gl, gl_ref)
+    assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
+    del st
+    torch.cuda.empty_cache()
