@@ -91,7 +91,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fg_tc.cu", "fg_simt.cu"):
+    for f in ("fg_tc.cu", "tc_common.cuh"):
         p = os.path.join(ROOT, "paper_1911_03813_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
