@@ -153,6 +153,57 @@ stmf_status stmf_profile_enable(stmf_ctx_t ctx, int32_t enable);
 stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* count_host);
 
 /*
+ * Optimiser options of stmf_fit. The paper (Sec. 4) runs L-BFGS-B without bounds, memory m = 5,
+ * at most 10,000 iterations and 50,000 function evaluations, and a gradient tolerance pgtol that
+ * varies by experiment (0.05 in Sec. 4.1, 1e-4 in Sec. 4.2). The other settings are this
+ * library's readings of the solver's defaults (strong-Wolfe line search with c1 = 1e-3, c2 = 0.9).
+ */
+typedef struct {
+  int32_t m;           /* number of stored correction pairs, 1..64 (paper: 5) */
+  int32_t max_ls;      /* evaluations per line search (20) */
+  double pgtol;        /* stop when max_i |g_i| <= pgtol */
+  double factr;        /* stop when the relative decrease of f <= factr * DBL_EPSILON (1e7); the
+                          decrease is measured against max(|f|, 1), so with F32/BF16/E4M3 samples,
+                          whose evaluations carry ~1e-7 relative noise in f, use factr >= 1e9 or 0 */
+  int64_t max_iters;   /* outer iterations (10,000) */
+  int64_t max_evals;   /* function/gradient evaluations (50,000) */
+  int32_t alpha_mode;  /* 1: f includes alpha = ||X||^2 (computed first); 0: shifted f, alpha = 0 */
+  int32_t chunk;       /* evaluations enqueued between host reads of the done flag (16) */
+} stmf_fit_opts;
+
+/* Outcome of stmf_fit (host struct). stop_reason: 1 pgtol, 2 factr, 3 max_iters, 4 max_evals,
+ * 5 line search failed, 6 non-finite value. status: the device status word (STMF_OK unless a
+ * kernel reported an error). */
+typedef struct {
+  double f;          /* objective at the returned iterate (includes alpha when alpha_mode = 1) */
+  double alpha;      /* ||X||^2 when alpha_mode = 1, else 0 */
+  double g_inf;      /* max |g_i| at the returned iterate */
+  int64_t iters;     /* outer iterations */
+  int64_t evals;     /* function/gradient evaluations ("inner iterations", Sec. 4.1) */
+  int32_t stop_reason;
+  int32_t status;
+} stmf_fit_result;
+
+/* Fill *opts with the defaults listed above (pgtol = 1e-5). */
+stmf_status stmf_fit_default_opts(stmf_fit_opts* opts);
+
+/*
+ * stmf_fit -- minimise f(lambda, A) = ||X - M||^2 (eq. optFunc) from the start (lambda, A) with
+ * the on-device L-BFGS described above; each evaluation is stmf_fg's Alg. 2. The optimiser state
+ * (iterate, gradient, m correction pairs, line-search points) stays in device memory; the host
+ * only reads a done flag once per `chunk` evaluations.
+ *  V, nu, d, r   as for stmf_fg.
+ *  opts          host pointer (see stmf_fit_default_opts).
+ *  lambda, A     device; the start on entry (r FP64; n x r FP64 column-major), the final iterate
+ *                on return.
+ *  out           host; the result.
+ * Synchronous: returns when the optimiser has stopped (work is issued on `stream`).
+ */
+stmf_status stmf_fit(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+                     int64_t r, const stmf_fit_opts* opts, double* lambda, double* A,
+                     stmf_fit_result* out, stmf_stream_t stream);
+
+/*
  * stmf_fg_noalloc -- the evaluation of stmf_fg for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface variant of stmf_fg (same kernels, same
  * arguments and results), added for callers such as code running inside a memory arena owned

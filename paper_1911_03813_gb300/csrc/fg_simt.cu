@@ -65,6 +65,7 @@ size_t smem_bytes(int n, int rp) {
 template <typename TC, int DT, int JB>
 __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
   using TS_t = typename Storage<DT>::T;
+  if (prm.skip && *prm.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = prm.n, r = prm.r, rp = prm.r_pad, d = prm.d, ld = prm.ld;
   const int vst = vstride_of(n);

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
   using C = Cfg<RP>;
   constexpr int N = C::N;
+  if (prm.skip && *prm.skip) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw_addr = tc::smem_addr(smem_raw);
   unsigned char* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);

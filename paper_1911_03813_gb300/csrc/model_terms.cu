@@ -29,6 +29,7 @@ constexpr int RY = 16;    // threads per entry
 constexpr int RMAX = 20;  // loads per thread (pass grid <= RY * RMAX = 320 blocks)
 
 __global__ void __launch_bounds__(RE * RY) reduce_kernel(const ModelParams prm, int L, int nb) {
+  if (prm.skip && *prm.skip) return;
   __shared__ double red[RY][RE];
   const int x = threadIdx.x % RE, y = threadIdx.x / RE;
   if ((int)blockIdx.x < nb) {
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(RE * RY) reduce_kernel(const ModelParams prm, 
 }
 
 __global__ void __launch_bounds__(RT) finalize_kernel(const ModelParams prm) {
+  if (prm.skip && *prm.skip) return;
   __shared__ double Cs[64 * 64];
   __shared__ double lam[64];
   __shared__ double us[64];

@@ -10,18 +10,6 @@
 
 #include "stmf_internal.h"
 
-struct stmf_ctx {
-  int device = 0;
-  int num_sms = 0;
-  void* ws = nullptr;        // device workspace (partials, reduced Y/w)
-  size_t ws_bytes = 0;
-  int32_t* status = nullptr; // device status word
-  std::string last_error;
-  bool profiling = false;    // record events around each fused pass
-  std::vector<cudaEvent_t> ev_pool;  // recorded pairs: [2k] start, [2k+1] end
-  size_t ev_used = 0;
-};
-
 namespace {
 
 constexpr size_t kMaxSmem = 232448;  // dynamic shared memory per block on sm_103
@@ -91,6 +79,90 @@ size_t gram_ws_bytes(int grid) { return size_t(grid) * sizeof(double); }
 
 }  // namespace
 
+stmf_status stmf::set_error(stmf_ctx* c, stmf_status st, const std::string& msg) {
+  return fail(c, st, msg);
+}
+stmf_status stmf::check_samples_arg(stmf_ctx* c, const stmf_samples* V) {
+  return check_samples(c, V);
+}
+stmf_status stmf::ensure_workspace(stmf_ctx* c, size_t bytes) { return ensure_ws(c, bytes); }
+size_t stmf::fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
+  return fg_ws_bytes(plan_fg(c, V, r), r);
+}
+
+stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
+                             const double* lambda, const double* A, const double* alpha, double* f,
+                             double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s) {
+  stmf_status st = check_samples(c, V);
+  if (st != STMF_OK) return st;
+  if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
+  if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
+  if (!lambda || !A || !f || !g_lambda || !G_A) return fail(c, STMF_EINVAL, "NULL model or output pointer");
+  const int n = (int)V->n;
+  const FgPlan pl = plan_fg(c, V, r);
+  if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
+    return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
+  st = ensure_ws(c, fg_ws_bytes(pl, r));
+  if (st != STMF_OK) return st;
+  double* partials = static_cast<double*>(c->ws);
+  double* yw = partials + pl.partial_doubles;
+
+  stmf::FgParams prm{};
+  prm.V = V->data;
+  prm.scale = V->scale;
+  prm.nu = nu;
+  prm.nu_uniform = 1.0 / double(V->p);
+  prm.A = A;
+  prm.partials = partials;
+  prm.p = V->p;
+  prm.n = n;
+  prm.ld = (int)V->ld;
+  prm.d = d;
+  prm.r = (int)r;
+  prm.r_pad = (int)((r + 3) / 4 * 4);
+  prm.flush_tiles = 16;
+  prm.status = c->status;
+  prm.skip = skip;
+  cudaEvent_t ev_end = nullptr;
+  if (c->profiling && c->ev_used + 2 <= 2 * 65536) {
+    while (c->ev_pool.size() < c->ev_used + 2) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) break;
+      c->ev_pool.push_back(ev);
+    }
+    if (c->ev_pool.size() >= c->ev_used + 2) {
+      cudaEventRecord(c->ev_pool[c->ev_used], s);
+      ev_end = c->ev_pool[c->ev_used + 1];
+      c->ev_used += 2;
+    }
+  }
+  cudaError_t e = pl.tc ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
+                        : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
+  if (ev_end) cudaEventRecord(ev_end, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fused pass launch");
+
+  stmf::ModelParams mp{};
+  mp.partials = partials;
+  mp.grid = pl.grid;
+  mp.A = A;
+  mp.lambda = lambda;
+  mp.alpha = alpha;
+  mp.f = f;
+  mp.g_lambda = g_lambda;
+  mp.G_A = G_A;
+  mp.yw = yw;
+  mp.bmat = yw + pl.L;
+  mp.n = n;
+  mp.r = (int)r;
+  mp.d = d;
+  mp.status = c->status;
+  mp.skip = skip;
+  e = stmf::model_terms_launch(mp, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "model terms launch");
+  return STMF_OK;
+}
+
+
 extern "C" {
 
 int stmf_version(void) { return 100; }
@@ -142,6 +214,7 @@ stmf_status stmf_destroy(stmf_ctx_t c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
+  if (c->fit_ws) cudaFree(c->fit_ws);
   if (c->status) cudaFree(c->status);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
@@ -178,72 +251,8 @@ stmf_status stmf_fg(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32
                     const double* lambda, const double* A, const double* alpha, double* f,
                     double* g_lambda, double* G_A, stmf_stream_t stream) {
   if (!c) return STMF_EINVAL;
-  stmf_status st = check_samples(c, V);
-  if (st != STMF_OK) return st;
-  if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
-  if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
-  if (!lambda || !A || !f || !g_lambda || !G_A) return fail(c, STMF_EINVAL, "NULL model or output pointer");
-  const int n = (int)V->n;
-  const FgPlan pl = plan_fg(c, V, r);
-  if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
-    return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
-  st = ensure_ws(c, fg_ws_bytes(pl, r));
-  if (st != STMF_OK) return st;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  double* partials = static_cast<double*>(c->ws);
-  double* yw = partials + pl.partial_doubles;
-
-  stmf::FgParams prm{};
-  prm.V = V->data;
-  prm.scale = V->scale;
-  prm.nu = nu;
-  prm.nu_uniform = 1.0 / double(V->p);
-  prm.A = A;
-  prm.partials = partials;
-  prm.p = V->p;
-  prm.n = n;
-  prm.ld = (int)V->ld;
-  prm.d = d;
-  prm.r = (int)r;
-  prm.r_pad = (int)((r + 3) / 4 * 4);
-  prm.flush_tiles = 16;
-  prm.status = c->status;
-  cudaEvent_t ev_end = nullptr;
-  if (c->profiling && c->ev_used + 2 <= 2 * 65536) {
-    while (c->ev_pool.size() < c->ev_used + 2) {
-      cudaEvent_t ev;
-      if (cudaEventCreate(&ev) != cudaSuccess) break;
-      c->ev_pool.push_back(ev);
-    }
-    if (c->ev_pool.size() >= c->ev_used + 2) {
-      cudaEventRecord(c->ev_pool[c->ev_used], s);
-      ev_end = c->ev_pool[c->ev_used + 1];
-      c->ev_used += 2;
-    }
-  }
-  cudaError_t e = pl.tc ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
-                        : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
-  if (ev_end) cudaEventRecord(ev_end, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "fused pass launch");
-
-  stmf::ModelParams mp{};
-  mp.partials = partials;
-  mp.grid = pl.grid;
-  mp.A = A;
-  mp.lambda = lambda;
-  mp.alpha = alpha;
-  mp.f = f;
-  mp.g_lambda = g_lambda;
-  mp.G_A = G_A;
-  mp.yw = yw;
-  mp.bmat = yw + pl.L;
-  mp.n = n;
-  mp.r = (int)r;
-  mp.d = d;
-  mp.status = c->status;
-  e = stmf::model_terms_launch(mp, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "model terms launch");
-  return STMF_OK;
+  return stmf::enqueue_fg(c, V, nu, d, r, lambda, A, alpha, f, g_lambda, G_A, nullptr,
+                          reinterpret_cast<cudaStream_t>(stream));
 }
 
 stmf_status stmf_profile_enable(stmf_ctx_t c, int32_t enable) {

@@ -23,6 +23,7 @@ struct FgParams {
   int r_pad;            // r rounded up to a multiple of 4
   int flush_tiles;      // FP32 accumulators are folded into FP64 every flush_tiles tiles
   int32_t* status;      // device status word
+  const int32_t* skip;  // when non-null and nonzero at launch, the kernel does nothing
 };
 
 // Finalisation of Alg. 2 lines 3-9 from the reduced (w, Y).
@@ -39,6 +40,7 @@ struct ModelParams {
   double* bmat;            // B = A^T A, r*r doubles (workspace)
   int n, r, d;
   int32_t* status;
+  const int32_t* skip;     // as in FgParams
 };
 
 struct GramParams {
@@ -76,6 +78,35 @@ inline int elem_bytes(int dtype) {
   }
 }
 
+}  // namespace stmf
+
+#include <vector>
+
+// A library context (opaque to callers): device, workspace, status word, timing events.
+struct stmf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  void* ws = nullptr;        // device workspace (partials, reduced Y/w)
+  size_t ws_bytes = 0;
+  void* fit_ws = nullptr;    // device workspace of the optimiser state
+  size_t fit_ws_bytes = 0;
+  int32_t* status = nullptr; // device status word
+  std::string last_error;
+  bool profiling = false;    // record events around each fused pass
+  std::vector<cudaEvent_t> ev_pool;  // recorded pairs: [2k] start, [2k+1] end
+  size_t ev_used = 0;
+};
+
+namespace stmf {
+// Shared host helpers of the entry points (stmf_api.cu).
+stmf_status set_error(stmf_ctx* c, stmf_status st, const std::string& msg);
+stmf_status check_samples_arg(stmf_ctx* c, const stmf_samples* V);
+stmf_status ensure_workspace(stmf_ctx* c, size_t bytes);
+// Enqueue one evaluation of Alg. 2 (fused pass + model terms) with optional skip flag.
+stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
+                       const double* lambda, const double* A, const double* alpha, double* f,
+                       double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s);
+size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
 }  // namespace stmf
 
 // Record a device-side error in the status word: the first error wins.

@@ -283,3 +283,67 @@ def fg_noalloc(V, nu, d, lam, A, alpha=None, out=None, status=None, stream=None)
         raise StmfError(st, "stmf_fg_noalloc")
     del keep
     return f, gl, GA
+
+
+class FitOpts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("max_ls", ctypes.c_int32), ("pgtol", ctypes.c_double),
+                ("factr", ctypes.c_double), ("max_iters", ctypes.c_int64),
+                ("max_evals", ctypes.c_int64), ("alpha_mode", ctypes.c_int32),
+                ("chunk", ctypes.c_int32)]
+
+
+class FitResult(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("alpha", ctypes.c_double), ("g_inf", ctypes.c_double),
+                ("iters", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("stop_reason", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+STOP_REASONS = {0: "running", 1: "pgtol", 2: "factr", 3: "max_iters", 4: "max_evals",
+                5: "line search failed", 6: "non-finite"}
+
+
+def _declare_fit(L):
+    vp = ctypes.c_void_p
+    L.stmf_fit_default_opts.argtypes = [ctypes.POINTER(FitOpts)]
+    L.stmf_fit_default_opts.restype = ctypes.c_int
+    L.stmf_fit.argtypes = [vp, ctypes.POINTER(Samples), vp, ctypes.c_int32, ctypes.c_int64,
+                           ctypes.POINTER(FitOpts), vp, vp, ctypes.POINTER(FitResult), vp]
+    L.stmf_fit.restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_fit)
+
+
+def fit_options(**kw):
+    """stmf_fit_opts with the library defaults, overridden by keyword arguments."""
+    o = FitOpts()
+    lib().stmf_fit_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def fit(V, nu, d, lam, A, opts=None, stream=None, ctx=None, **kw):
+    """stmf_fit: on-device L-BFGS from the start (lam, A); lam (r,) and A (n, r, column-major)
+    are CUDA float64 tensors updated in place with the final iterate. Returns a dict."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    n, r = desc.n, lam.shape[0]
+    _check_f64(lam, (r,), "lambda")
+    if A.dtype != torch.float64 or not A.is_cuda or tuple(A.shape) != (n, r):
+        raise ValueError("A must be an (n, r) CUDA float64 tensor")
+    if not ((A.stride(0) == 1 or n == 1) and (A.stride(1) == n or r == 1)):
+        raise ValueError("A must be column-major (A.stride() == (1, n))")
+    if nu is not None:
+        _check_f64(nu, (desc.p,), "nu")
+    o = opts if opts is not None else fit_options(**kw)
+    res = FitResult()
+    st = lib().stmf_fit(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d), int(r), ctypes.byref(o),
+                        _ptr(lam), _ptr(A), ctypes.byref(res), _stream(stream))
+    ctx.check(st, "stmf_fit")
+    del keep
+    return dict(f=res.f, alpha=res.alpha, g_inf=res.g_inf, iters=res.iters, evals=res.evals,
+                stop=res.stop_reason, stop_name=STOP_REASONS.get(res.stop_reason, "?"),
+                status=res.status)
