@@ -1,0 +1,101 @@
+"""The autograd.Function over (lambda, A) (-m gpu).
+
+Differentiation workload: n = 64, d = 3, r = 8, p = 1e6 FP32 Gaussian-mixture samples. The
+objective is wrapped in an outer loss L = f(lambda, A) + sum_j (||a_j|| - 1)^2; its autograd
+gradient is checked against central finite differences (step 1e-3) along 200 random unit
+directions and against the oracle's gradient; backward is timed against forward.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1911_03813_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_03813_gb300 import autograd, stmf
+    torch.cuda.set_device(0)
+    n, p, r, d = 64, 1000000, 8, 3
+    st = inputs.gmm_device(n, p, r, 0.1, seed=404, device="cuda", out_dtype="f32")
+    lam0, A0 = inputs.random_model(n, r, seed=405)
+    return dict(autograd=autograd, stmf=stmf, st=st, lam0=lam0, A0=A0, n=n, r=r, d=d)
+
+
+def outer_loss(ag, st, lam, A, d):
+    f = ag.objective(lam, A, st, None, d)
+    return f + ((A.norm(dim=0) - 1.0) ** 2).sum()
+
+
+def test_autograd_matches_oracle_and_finite_differences(setup):
+    ag, st, d = setup["autograd"], setup["st"], setup["d"]
+    n, r = setup["n"], setup["r"]
+    lam = torch.tensor(setup["lam0"], device="cuda", requires_grad=True)
+    A = torch.tensor(setup["A0"], device="cuda", requires_grad=True)   # row-major on purpose
+    L = outer_loss(ag, st, lam, A, d)
+    L.backward()
+    g = torch.cat([lam.grad, A.grad.t().reshape(-1)]).cpu().numpy()
+    # the oracle's gradient of the same outer loss, on the FP32 values the GPU reads
+    data = st["data"][:, :n]
+
+    def cols(c0, c1):
+        return data[c0:c1].double().cpu().numpy().T
+
+    p = data.shape[0]
+    _, gl_o, GA_o = oracle.fg_implicit(None, cols, setup["lam0"], setup["A0"], d, p=p)
+    A0 = setup["A0"]
+    nrm = np.linalg.norm(A0, axis=0)
+    GA_o = GA_o + 2.0 * (nrm - 1.0) / nrm * A0
+    g_o = np.concatenate([gl_o, GA_o.T.reshape(-1)])
+    assert np.linalg.norm(g - g_o) <= 1e-5 * np.linalg.norm(g_o)
+    # central differences along 200 unit directions, step 1e-3
+    x0 = np.concatenate([setup["lam0"], A0.T.reshape(-1)])
+    rng = np.random.default_rng(7)
+    h = 1e-3
+    worst = 0.0
+    with torch.no_grad():
+        def L_at(x):
+            lam_x = torch.tensor(x[:r], device="cuda")
+            A_x = torch.tensor(x[r:].reshape(r, n).T.copy(), device="cuda")
+            return float(outer_loss(ag, st, lam_x, A_x, d))
+        for _ in range(200):
+            delta = rng.standard_normal(x0.size)
+            delta /= np.linalg.norm(delta)
+            fd = (L_at(x0 + h * delta) - L_at(x0 - h * delta)) / (2 * h)
+            an = float(g @ delta)
+            err = abs(fd - an)
+            worst = max(worst, err / (1e-3 * abs(an) + 1e-6))
+            assert err <= 1e-3 * abs(an) + 1e-6, (fd, an)
+    print("worst FD error / band: %.3f" % worst)
+
+
+def test_backward_is_cheap_against_forward(setup):
+    ag, st, d = setup["autograd"], setup["st"], setup["d"]
+    lam = torch.tensor(setup["lam0"], device="cuda", requires_grad=True)
+    A = torch.tensor(setup["A0"], device="cuda", requires_grad=True)
+    for _ in range(3):
+        f = ag.objective(lam, A, st, None, d)
+        f.backward()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for _ in range(20):
+        lam.grad = None
+        A.grad = None
+        torch.cuda.synchronize()
+        e[0].record()
+        f = ag.objective(lam, A, st, None, d)
+        e[1].record()
+        f.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd += e[0].elapsed_time(e[1])
+        bwd += e[1].elapsed_time(e[2])
+    print("forward %.3f ms, backward %.3f ms per call" % (fwd / 20, bwd / 20))
+    assert bwd < 0.25 * fwd
