@@ -287,7 +287,9 @@ stmf_status stmf_norm_x(stmf_ctx_t c, const stmf_samples* V, const double* nu, i
   if (!alpha_out) return fail(c, STMF_EINVAL, "alpha_out is NULL");
   if (V->dtype == STMF_F64 && V->n > 200)
     return fail(c, STMF_EINVAL, "FP64 samples: n must be <= 200 for the Gram pass");
-  const int grid = stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);
+  const bool tc = stmf::gram_tc_supported(V->dtype, (int)V->n, V->p);
+  const int grid = tc ? stmf::gram_tc_grid(V->p, c->num_sms)
+                      : stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);
   st = ensure_ws(c, gram_ws_bytes(grid));
   if (st != STMF_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -302,7 +304,8 @@ stmf_status stmf_norm_x(stmf_ctx_t c, const stmf_samples* V, const double* nu, i
   gp.ld = (int)V->ld;
   gp.d = d;
   gp.status = c->status;
-  cudaError_t e = stmf::gram_simt_launch(V->dtype, gp, grid, s);
+  cudaError_t e = tc ? stmf::gram_tc_launch(gp, grid, s)
+                     : stmf::gram_simt_launch(V->dtype, gp, grid, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Gram pass launch");
   e = stmf::reduce_scalar_launch(gp.partials, grid, alpha_out, c->status, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Gram reduction launch");

@@ -64,6 +64,9 @@ int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s);
 int gram_simt_grid(int dtype, int n, int64_t p, int num_sms);
+bool gram_tc_supported(int dtype, int n, int64_t p);
+int gram_tc_grid(int64_t p, int num_sms);
+cudaError_t gram_tc_launch(const GramParams& prm, int grid, cudaStream_t s);
 cudaError_t gram_simt_launch(int dtype, const GramParams& prm, int grid, cudaStream_t s);
 cudaError_t reduce_scalar_launch(const double* partials, int count, double* out,
                                  int32_t* status, cudaStream_t s);

@@ -211,3 +211,19 @@ def test_fg_full_size(stmf, dtype, n, p, r, d, sigma):
     assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,p,d,weights", [(256, 1 << 15, 4, None), (100, 20000, 3, None),
+                                           (64, 9000, 2, "nonuniform"), (33, 3001, 4, "nonuniform"),
+                                           (256, 1200, 3, None), (17, 129, 4, None)])
+def test_norm_x_tensor_core_parity(stmf, n, p, d, weights):
+    """BF16 samples take the tensor-core Gram pass: several J chunks, ragged tiles, nu given."""
+    data = inputs.gmm(n, p, 8, 0.1, seed=n + p)
+    st = inputs.to_storage(data["V"], "bf16", device="cuda")
+    nu = inputs.positive_weights(p, seed=p) if weights else None
+    nu_t = None if nu is None else torch.tensor(nu, device="cuda")
+    ref = oracle.norm_x(nu, decoded(st).T, d)
+    got = stmf.norm_x(st, nu_t, d).item()
+    torch.cuda.synchronize()
+    assert stmf.default_context().device_status() == 0
+    assert abs(got - ref) <= 2e-6 * abs(ref), (got, ref)
