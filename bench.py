@@ -184,7 +184,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=P_FULL)
-    ap.add_argument("--legs", default="bf16,fp32", help="sample types to time (bf16 is the headline)")
+    ap.add_argument("--legs", default="bf16,fp32,fp8",
+                    help="sample types to time (bf16 is the headline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -219,6 +220,9 @@ def main():
     else:
         st16 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="bf16")
         st32 = None
+    st8 = None
+    if "fp8" in legs:
+        st8 = inputs.gmm_device(N_FEAT, P, N_MEANS, SIGMA, SEED + rank, dev, out_dtype="e4m3")
     lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
     lam_t = torch.tensor(lam, device=dev)
     A_t = torch.tensor(A.T.copy(), device=dev).T
@@ -226,6 +230,8 @@ def main():
     stmf.reserve(st16, R)
     if st32 is not None:
         stmf.reserve(st32, R)
+    if st8 is not None:
+        stmf.reserve(st8, R)
     f = torch.empty(1, dtype=torch.float64, device=dev)
     gl = torch.empty(R, dtype=torch.float64, device=dev)
     GA = torch.empty((R, N_FEAT), dtype=torch.float64, device=dev).T
@@ -258,6 +264,9 @@ def main():
         ms32, pass32 = timed(st32, max(args.steps // 2, 1), args.warmup, prof=True)
     else:
         ms32 = pass32 = float("nan")
+    ms8 = pass8 = float("nan")
+    if st8 is not None:
+        ms8, pass8 = timed(st8, args.steps, args.warmup, prof=True)
     with ClockSampler(local) as clk:
         ms16, pass16 = timed(st16, args.steps, args.warmup, prof=True)
     if world > 1:
@@ -332,6 +341,11 @@ def main():
                  "ms_per_step": ms32 / steps32, "hbm_gbs_over_V": bytes32 / (ms32 / steps32 / 1e3) / 1e9,
                  "pass_frac_of_hbm": ach32 / peaks["hbm_gbs"],
                  "bf16_over_fp32": (args.steps / ms16) / (steps32 / ms32)},
+        "fp8": {"value": args.steps / (ms8 / 1e3) * world, "unit": "evals/s",
+                "ms_per_step": ms8 / args.steps,
+                "pass_gbs_over_V": P * (N_FEAT + 4) / (pass8 / 1e3) / 1e9,
+                "pass_frac_of_hbm": P * (N_FEAT + 4) / (pass8 / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "storage": "E4M3 codes + one FP32 scale per sample"},
         "clocks": clk.summary(),
         "gpu_launches": 3 * (args.steps + max(args.steps // 2, 1)),
         "e2e": e2e,

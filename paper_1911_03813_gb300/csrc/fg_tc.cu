@@ -27,6 +27,8 @@
 // and free TMEM before the CTA exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "stmf_internal.h"
 #include "tc_common.cuh"
@@ -39,6 +41,9 @@ constexpr int REG_BYTES = TM * 128;    // one 64-feature region of a V tile (16 
 constexpr int EG = 4;                  // epilogue warpgroups (components split among them)
 constexpr int NEPI = 128 * EG;         // epilogue threads
 constexpr int NTHREADS = 96 + NEPI;    // producer warp, MMA1 warp, MMA2 warp, epilogue
+constexpr int NCONV = 4;               // FP8 samples: warps that widen E4M3 tiles to BF16
+constexpr int NTHREADS_FP8 = NTHREADS + 32 * NCONV;
+constexpr int Q_BYTES = TM * 128;      // one 128-feature region of an E4M3 tile (16 KB)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
 struct TcExtra {
@@ -48,6 +53,8 @@ struct TcExtra {
   int flush;      // tiles between folds of Y into FP64
   int tmem_cols;
   int smem_bytes;
+  int nq;         // E4M3 samples: 128-feature regions per tile (ceil(n / 128))
+  int qstages;    // E4M3 samples: TMA ring depth of E4M3 tiles
 };
 
 template <int RP>
@@ -82,9 +89,15 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
   }
 }
 
-template <int RP>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// FP8 = false: BF16 samples, TMA fills the S-stage ring the MMAs read.
+// FP8 = true:  E4M3 samples (v = s q), TMA fills a ring of E4M3 tiles, NCONV converter warps widen
+//              each tile into one of two BF16 buffers (S = 2) that the MMAs read (every E4M3 value
+//              is exactly a BF16 value), and the scale folds into the weight, nu' = nu s^d: with
+//              z = q^T a, the terms of eq. Y and Lemma 3.5 are nu' z^{d-1} q and nu' z^d.
+template <int RP, bool FP8>
+__global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
+  constexpr int NT = FP8 ? NTHREADS_FP8 : NTHREADS;
   using C = Cfg<RP>;
   constexpr int N = C::N;
   if (prm.skip && *prm.skip) return;
@@ -98,7 +111,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   unsigned char* sV = base;
   unsigned char* sW = sV + size_t(S) * stage_bytes;
   unsigned char* sA = sW + 2 * 2 * C::W_REG;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nreg) * C::A_REG);
+  unsigned char* sQ = sA + size_t(nreg) * C::A_REG;  // E4M3 ring (FP8 only)
+  const int QS = FP8 ? ex.qstages : 0, nq = ex.nq;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + size_t(QS) * nq * Q_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
   uint64_t* zfull = bars + 2 * S;
@@ -111,13 +126,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   double* wred = reinterpret_cast<double*>(mma_done + 3);  // 4 x RP
+  uint64_t* qfull = reinterpret_cast<uint64_t*>(wred + 4 * RP);  // FP8 only
+  uint64_t* qempty = qfull + QS;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&full[s], FP8 ? NCONV : 1);  // TMA arrival, or one per converter warp
       tc::mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < QS; ++s) {
+      tc::mbar_init(&qfull[s], 1);
+      tc::mbar_init(&qempty[s], NCONV);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&zfull[b], 1);
@@ -138,7 +159,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // A split: rows [0, RP) hold BF16(a_j), rows [RP, 2 RP) hold BF16(a_j - BF16(a_j)); K = feature.
   {
     const int kext = nreg * 64;
-    for (int e = tid; e < N * kext; e += NTHREADS) {
+    for (int e = tid; e < N * kext; e += NT) {
       const int row = e / kext, k = e - row * kext;
       const int j = row % RP;
       double a = (j < r && k < n) ? prm.A[k + size_t(n) * j] : 0.0;
@@ -152,7 +173,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int words = zero_regs * REG_BYTES / 16;
       for (int s = 0; s < S; ++s) {
         uint4* z = reinterpret_cast<uint4*>(sV + size_t(s) * stage_bytes + size_t(nload) * REG_BYTES);
-        for (int e = tid; e < words; e += NTHREADS) z[e] = make_uint4(0, 0, 0, 0);
+        for (int e = tid; e < words; e += NT) z[e] = make_uint4(0, 0, 0, 0);
       }
     }
   }
@@ -176,24 +197,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
+      // BF16: tiles go straight into the MMA ring; E4M3: into the E4M3 ring for the converters
+      const int R = FP8 ? QS : S;
+      uint64_t* rfull = FP8 ? qfull : full;
+      uint64_t* rempty = FP8 ? qempty : empty;
+      const uint32_t rbytes = FP8 ? uint32_t(nq) * Q_BYTES : uint32_t(nload) * REG_BYTES;
       int issued = 0;
       for (int it = 0; it < my_tiles; ++it) {
-        const int st = it % S;
-        const uint32_t ph = (it / S) & 1;
-        if (!tc::mbar_wait(&empty[st], ph ^ 1, abortv, WAIT_LIMIT)) {
+        const int st = it % R;
+        const uint32_t ph = (it / R) & 1;
+        if (!tc::mbar_wait(&rempty[st], ph ^ 1, abortv, WAIT_LIMIT)) {
           fail();
           break;
         }
-        tc::mbar_arrive_expect_tx(&full[st], uint32_t(nload) * REG_BYTES);
+        tc::mbar_arrive_expect_tx(&rfull[st], rbytes);
         const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
-        for (int g = 0; g < nload; ++g)
-          tc::tma_load_2d(sV + size_t(st) * stage_bytes + size_t(g) * REG_BYTES, &tmap, g * 64,
-                          (int32_t)(tile * TM), &full[st]);
+        if constexpr (FP8) {
+          for (int g = 0; g < nq; ++g)
+            tc::tma_load_2d(sQ + (size_t(st) * nq + g) * Q_BYTES, &tmap, g * 128,
+                            (int32_t)(tile * TM), &rfull[st]);
+        } else {
+          for (int g = 0; g < nload; ++g)
+            tc::tma_load_2d(sV + size_t(st) * stage_bytes + size_t(g) * REG_BYTES, &tmap, g * 64,
+                            (int32_t)(tile * TM), &rfull[st]);
+        }
         ++issued;
       }
       // wait for the last copy issued into each stage (already complete unless we aborted)
-      for (int k = issued > S ? issued - S : 0; k < issued; ++k)
-        tc::mbar_wait(&full[k % S], (k / S) & 1, &no_abort, WAIT_LIMIT);
+      for (int k = issued > R ? issued - R : 0; k < issued; ++k)
+        tc::mbar_wait(&rfull[k % R], (k / R) & 1, &no_abort, WAIT_LIMIT);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA1 issuer
@@ -258,6 +290,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mma_commit(&mma_done[1]);
       tc::mbar_wait(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
     }
+  } else if (FP8 && warp >= 3 + NEPI / 32) {
+    // ------------------------------------------------------------------ E4M3 -> BF16 converters
+    // Tile t: E4M3 region g (features [128 g, 128 g + 128), 128-byte rows) becomes BF16 regions
+    // 2g and 2g + 1 of MMA buffer t % 2, both in the 128-byte swizzle. Features beyond n are zero
+    // (TMA fills them), so the BF16 padding is zero too.
+    if constexpr (FP8) {
+      const int ct = tid - (96 + NEPI);
+      const int chunks = nq * TM * 8;  // 16-byte chunks per E4M3 tile
+      bool ok = true;
+      for (int it = 0; it < my_tiles; ++it) {
+        const int qs = it % QS, b = it % S;
+        if (!tc::mbar_wait(&qfull[qs], (it / QS) & 1, abortv, WAIT_LIMIT) ||
+            !tc::mbar_wait(&empty[b], ((it / S) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* src = sQ + size_t(qs) * nq * Q_BYTES;
+        unsigned char* dst = sV + size_t(b) * stage_bytes;
+        for (int e = ct; e < chunks; e += 32 * NCONV) {
+          const int g = e >> 10, y = (e >> 3) & 127, c8 = e & 7;
+          const uint4 raw = *reinterpret_cast<const uint4*>(
+              src + size_t(g) * Q_BYTES + y * 128 + (((c8 ^ (y & 7)) & 7) << 4));
+          const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+          uint32_t outw[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(
+                  (__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+              const __half2 hh = *reinterpret_cast<const __half2*>(&hr);
+              const __nv_bfloat162 bb = __floats2bfloat162_rn(__low2float(hh), __high2float(hh));
+              outw[2 * k + h] = *reinterpret_cast<const uint32_t*>(&bb);
+            }
+          }
+          // 16 features = two 16-byte chunks of BF16 region 2g + c8/4, chunks 2 (c8 % 4) + {0,1}
+          unsigned char* reg = dst + size_t(2 * g + (c8 >> 2)) * REG_BYTES + y * 128;
+          const int c16 = (c8 & 3) * 2;
+          *reinterpret_cast<uint4*>(reg + (((c16 ^ (y & 7)) & 7) << 4)) =
+              make_uint4(outw[0], outw[1], outw[2], outw[3]);
+          *reinterpret_cast<uint4*>(reg + ((((c16 + 1) ^ (y & 7)) & 7) << 4)) =
+              make_uint4(outw[4], outw[5], outw[6], outw[7]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(&full[b]);
+          tc::mbar_arrive(&qempty[qs]);
+        }
+      }
+      if (!ok) fail();
+    }
   } else {
     // ------------------------------------------------------------------ epilogue
     // EG warpgroups; warpgroup g owns components [g*CPG, (g+1)*CPG) of every sample of the tile
@@ -320,7 +404,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
       const int64_t sidx = tile * TM + L;
       float nu_s = 0.f;
-      if (sidx < prm.p) nu_s = prm.nu ? (float)prm.nu[sidx] : (float)prm.nu_uniform;
+      if (sidx < prm.p) {
+        double nu_d = prm.nu ? prm.nu[sidx] : prm.nu_uniform;
+        if constexpr (FP8) {  // nu' = nu s^d (the scale of sample l folded into its weight)
+          const double sc = (double)prm.scale[sidx];
+          double sd = sc;
+          for (int e = 1; e < d; ++e) sd *= sc;
+          nu_d *= sd;
+        }
+        nu_s = (float)nu_d;
+      }
       if (!tc::mbar_wait(&zfull[zb], (it >> 1) & 1, abortv, WAIT_LIMIT)) {
         ok = false;
         break;
@@ -430,7 +523,7 @@ EncodeFn get_encode() {
 
 int rp_of(int r) { return r <= 8 ? 8 : 16; }
 
-TcExtra plan(int n, int r) {
+TcExtra plan(int n, int r, bool fp8) {
   TcExtra ex{};
   ex.nload = (n + 63) / 64;
   ex.nreg = 2 * ((n + 127) / 128);
@@ -446,31 +539,42 @@ TcExtra plan(int n, int r) {
   while (pow2 < cols) pow2 <<= 1;
   ex.tmem_cols = pow2;
   ex.smem_bytes = fixed + S * stage;
+  ex.nq = (n + 127) / 128;
+  ex.qstages = 0;
+  if (fp8) {
+    // two BF16 buffers for the MMAs, the rest of shared memory for the E4M3 ring
+    ex.stages = 2;
+    const int qstage = ex.nq * Q_BYTES;
+    int QS = (232448 - fixed - 2 * stage - 64 * 8) / qstage;
+    if (QS > 6) QS = 6;
+    ex.qstages = QS;
+    ex.smem_bytes = fixed + 2 * stage + QS * qstage + 64 * 8;
+  }
   return ex;
 }
 
-template <int RP>
+template <int RP, bool FP8>
 cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtra& ex, int grid,
                       cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_tc_kernel<RP>,
+    cudaError_t e = cudaFuncSetAttribute(fg_tc_kernel<RP, FP8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_tc_kernel<RP><<<grid, NTHREADS, ex.smem_bytes, s>>>(tmap, prm, ex);
+  fg_tc_kernel<RP, FP8><<<grid, FP8 ? NTHREADS_FP8 : NTHREADS, ex.smem_bytes, s>>>(tmap, prm, ex);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t fg_tc_supported(int dtype, int n, int r) {
-  if (dtype != STMF_BF16) return 0;
+  if (dtype != STMF_BF16 && dtype != STMF_E4M3) return 0;
   if (r < 1 || r > 16 || n < 1 || n > 256) return 0;
   if (!get_encode()) return 0;
-  const TcExtra ex = plan(n, r);
-  return ex.stages >= 2 ? 1 : 0;
+  const TcExtra ex = plan(n, r, dtype == STMF_E4M3);
+  return (dtype == STMF_E4M3 ? ex.qstages >= 2 : ex.stages >= 2) ? 1 : 0;
 }
 
 int fg_tc_grid(int, int, int, int64_t p, int num_sms) {
@@ -479,22 +583,28 @@ int fg_tc_grid(int, int, int, int64_t p, int num_sms) {
 }
 
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
-  if (dtype != STMF_BF16) return cudaErrorNotSupported;
+  if (dtype != STMF_BF16 && dtype != STMF_E4M3) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
   EncodeFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
+  const bool fp8 = dtype == STMF_E4M3;
   CUtensorMap tmap;
   const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
-  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * 2};
-  const cuuint32_t box[2] = {64, TM};
+  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * (fp8 ? 1 : 2)};
+  const cuuint32_t box[2] = {fp8 ? 128u : 64u, TM};  // 128-byte rows either way
   const cuuint32_t estr[2] = {1, 1};
-  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(prm.V), dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult cr = enc(&tmap, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                    2, const_cast<void*>(prm.V), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const TcExtra ex = plan(prm.n, prm.r);
-  if (rp_of(prm.r) == 8) return launch_rp<8>(tmap, prm, ex, grid, s);
-  return launch_rp<16>(tmap, prm, ex, grid, s);
+  const TcExtra ex = plan(prm.n, prm.r, fp8);
+  if (fp8) {
+    if (rp_of(prm.r) == 8) return launch_rp<8, true>(tmap, prm, ex, grid, s);
+    return launch_rp<16, true>(tmap, prm, ex, grid, s);
+  }
+  if (rp_of(prm.r) == 8) return launch_rp<8, false>(tmap, prm, ex, grid, s);
+  return launch_rp<16, false>(tmap, prm, ex, grid, s);
 }
 
 }  // namespace stmf
