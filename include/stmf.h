@@ -203,6 +203,89 @@ stmf_status stmf_fit(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, in
                      int64_t r, const stmf_fit_opts* opts, double* lambda, double* A,
                      stmf_fit_result* out, stmf_stream_t stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: continuously batched fits (not part of the paper; a request is a fit of Sec. 4 with
+ * several starts, of which the best final f is kept, as in Sec. 4.2's best-of-ten protocol).
+ *
+ * A server owns a scheduler thread and `max_fits` fit slots (a context, a CUDA stream and
+ * preallocated workspaces each). Each start of a request occupies one slot and runs the
+ * on-device L-BFGS of stmf_fit. Requests are admitted first-come first-served as soon as enough
+ * slots are free and their device footprint fits the memory budget; fits of different requests
+ * run at the same time on their own streams, so work that arrives while others run overlaps with
+ * them on the GPU. Each fit's kernels use a fixed launch shape and fixed-order reductions, so a
+ * result does not depend on what else is running.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct stmf_server* stmf_server_t;
+
+typedef struct {
+  int32_t device;
+  int32_t max_fits;      /* fit slots (concurrent starts), >= 1 */
+  int32_t n_max;         /* largest n of any request (<= 256) */
+  int32_t r_max;         /* largest r of any request (<= 64) */
+  int32_t m_max;         /* largest L-BFGS memory of any request */
+  int32_t reserved;
+  size_t mem_budget;     /* device bytes: slot workspaces + admitted requests' footprints */
+} stmf_server_config;
+
+typedef struct {
+  stmf_samples V;          /* data: device pointers, or host pointers when V_on_host = 1 */
+  int32_t V_on_host;       /* 1: V.data (and V.scale) are host memory; the server copies them to
+                              device memory it allocates at admission and frees at completion */
+  int32_t d;
+  int64_t r;
+  int32_t n_starts;        /* >= 1 */
+  int32_t reserved;
+  const double* nu;        /* device p FP64 or NULL (1/p); must stay valid until completion */
+  const double* x0;        /* host: n_starts start points, each [lambda (r); A (n x r, col-major)] */
+  double* lambda_out;      /* device, r: best start's final lambda (NULL: not copied) */
+  double* A_out;           /* device, n x r: best start's final A (NULL: not copied) */
+  stmf_fit_opts opts;
+} stmf_request;
+
+typedef struct {
+  int32_t state;           /* STMF_OK (done), STMF_ENOTREADY, STMF_ECANCELLED, or an error */
+  int32_t best_start;
+  stmf_fit_result best;    /* result of the start with the lowest final f */
+  int64_t total_evals;     /* evaluations over all starts */
+  double t_submit, t_admit, t_done;  /* seconds on the server's clock */
+  size_t footprint;        /* device bytes charged to the request at admission */
+} stmf_request_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, cancelled, failed;
+  int32_t active_fits, queued;
+  size_t bytes_in_use;     /* admitted footprints (excluding slot workspaces) */
+  size_t peak_bytes_in_use;
+  size_t slot_bytes;       /* preallocated slot workspaces */
+  double now;              /* server clock, seconds */
+} stmf_server_stats;
+
+/* Create a server: allocates max_fits slots (fails with STMF_ENOMEM when they alone exceed
+ * mem_budget) and starts the scheduler thread. */
+stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_server_t* out);
+
+/* Stop the scheduler (running requests are cancelled), free everything. */
+stmf_status stmf_server_destroy(stmf_server_t srv);
+
+/* Queue a request. The struct and the start points x0 are copied at submission; samples given
+ * in host memory (V_on_host = 1) are copied to the device at admission, so they (and device
+ * samples, nu and the output buffers) must stay valid until the request has finished.
+ * *ticket identifies the request. STMF_EINVAL for invalid arguments; STMF_ENOMEM when its
+ * footprint alone exceeds what the budget leaves after the slots. */
+stmf_status stmf_submit(stmf_server_t srv, const stmf_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: no limit) for the request; fills *out (host) and
+ * returns STMF_OK once it has finished (successfully or not: see out->state), STMF_ENOTREADY
+ * while it is queued or running, STMF_EINVAL for an unknown ticket. */
+stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_request_result* out,
+                      int32_t timeout_ms);
+
+/* Cancel a queued or running request; it finishes with state STMF_ECANCELLED. */
+stmf_status stmf_cancel(stmf_server_t srv, uint64_t ticket);
+
+/* Counters of the server (host struct). */
+stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats* out);
+
 /*
  * stmf_fg_noalloc -- the evaluation of stmf_fg for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface variant of stmf_fg (same kernels, same

@@ -405,9 +405,13 @@ __global__ void fit_export(FitLayout L, double* lambda, double* A, int r, long l
   }
 }
 
-size_t fit_bytes(long long D, int m) {
+}  // namespace
+
+size_t fit_state_bytes(long long D, int m) {
   return 256 + sizeof(double) * (size_t(D) * (7 + 2 * size_t(m)) + size_t(m) + 8);
 }
+
+namespace {
 
 FitLayout layout(void* base, long long D, int m) {
   FitLayout L;
@@ -429,6 +433,106 @@ FitLayout layout(void* base, long long D, int m) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------- host side
+
+stmf_status FitRun::begin(stmf_ctx* c, const stmf_samples* V_, const double* nu_, int d_,
+                          int64_t r_, const stmf_fit_opts* o, double* lambda, double* A,
+                          cudaStream_t s) {
+  ctx = c;
+  V = *V_;
+  nu = nu_;
+  d = d_;
+  r = r_;
+  opts = *o;
+  lam_out = lambda;
+  A_out = A;
+  stream = s;
+  D = r + V.n * r;
+  stmf_status st = check_samples_arg(c, &V);
+  if (st != STMF_OK) return st;
+  if (d < 2 || d > 8) return set_error(c, STMF_EINVAL, "d must be in [2, 8]");
+  if (r < 1 || r > 64) return set_error(c, STMF_EINVAL, "r must be in [1, 64]");
+  if (o->m < 1 || o->m > 64 || o->max_ls < 1 || o->chunk < 1 || o->max_evals < 1 ||
+      o->max_iters < 0 || !(o->pgtol >= 0.0) || !(o->factr >= 0.0))
+    return set_error(c, STMF_EINVAL, "invalid optimiser options");
+  st = ensure_workspace(c, fg_workspace_bytes(c, &V, r));
+  if (st != STMF_OK) return st;
+  const size_t need = fit_state_bytes(D, o->m);
+  if (need > c->fit_ws_bytes) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_error(c, STMF_ECUDA, "sync");
+    if (c->fit_ws) cudaFree(c->fit_ws);
+    c->fit_ws = nullptr;
+    c->fit_ws_bytes = 0;
+    if (cudaMalloc(&c->fit_ws, need) != cudaSuccess)
+      return set_error(c, STMF_ENOMEM, "cudaMalloc of the optimiser state failed");
+    c->fit_ws_bytes = need;
+  }
+  FitLayout L = layout(c->fit_ws, D, o->m);
+  fit_init<<<32, 256, 0, s>>>(L, lambda, A, (int)r, D);
+  if (cudaGetLastError() != cudaSuccess) return set_error(c, STMF_ECUDA, "fit_init launch");
+  if (o->alpha_mode) {
+    st = stmf_norm_x(c, &V, nu, d, &L.st->alpha, reinterpret_cast<stmf_stream_t>(s));
+    if (st != STMF_OK) return st;
+  }
+  enqueued = 0;
+  return STMF_OK;
+}
+
+stmf_status FitRun::enqueue_chunk(int32_t* done_host) {
+  FitLayout L = layout(ctx->fit_ws, D, opts.m);
+  StepOpts so;
+  so.pgtol = opts.pgtol;
+  so.factr = opts.factr;
+  so.c1 = 1e-3;
+  so.c2 = 0.9;
+  so.max_iters = opts.max_iters;
+  so.max_evals = opts.max_evals;
+  so.max_ls = opts.max_ls;
+  const int32_t* skip = &L.st->done;
+  for (int k = 0; k < opts.chunk; ++k) {
+    stmf_status st = enqueue_fg(ctx, &V, nu, d, r, L.xt, L.xt + r, &L.st->alpha, &L.st->ft,
+                                L.gt, L.gt + r, skip, stream);
+    if (st != STMF_OK) return st;
+    lbfgs_step<<<1, LT, 0, stream>>>(L, so);
+    if (cudaGetLastError() != cudaSuccess) return set_error(ctx, STMF_ECUDA, "lbfgs_step launch");
+  }
+  enqueued += opts.chunk;
+  if (cudaMemcpyAsync(done_host, &L.st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) !=
+      cudaSuccess)
+    return set_error(ctx, STMF_ECUDA, "reading the done flag");
+  return STMF_OK;
+}
+
+bool FitRun::exhausted() const { return enqueued > opts.max_evals + opts.chunk; }
+
+stmf_status FitRun::finish(void* state_host) {
+  FitLayout L = layout(ctx->fit_ws, D, opts.m);
+  fit_export<<<32, 256, 0, stream>>>(L, lam_out, A_out, (int)r, D);
+  if (cudaGetLastError() != cudaSuccess) return set_error(ctx, STMF_ECUDA, "fit_export launch");
+  if (cudaMemcpyAsync(state_host, L.st, sizeof(FitState), cudaMemcpyDeviceToHost, stream) !=
+      cudaSuccess)
+    return set_error(ctx, STMF_ECUDA, "reading the optimiser state");
+  return STMF_OK;
+}
+
+size_t FitRun::state_size() { return sizeof(FitState); }
+
+void FitRun::result_from(const void* state_host, int32_t dev_status, stmf_fit_result* out) {
+  const FitState& h = *static_cast<const FitState*>(state_host);
+  out->f = h.f;
+  out->alpha = h.alpha;
+  out->g_inf = h.g_inf;
+  out->iters = h.iters;
+  out->evals = h.evals;
+  out->stop_reason = h.stop;
+  out->status = dev_status;
+}
+
+size_t fit_workspace_total(const stmf_ctx* c, const stmf_samples* V, int64_t r, int m) {
+  return fg_workspace_bytes(c, V, r) + fit_state_bytes(r + V->n * r, m);
+}
+
 }  // namespace stmf
 
 extern "C" stmf_status stmf_fit_default_opts(stmf_fit_opts* o) {
@@ -450,76 +554,26 @@ extern "C" stmf_status stmf_fit(stmf_ctx_t c, const stmf_samples* V, const doubl
                                 stmf_stream_t stream) {
   using namespace stmf;
   if (!c) return STMF_EINVAL;
-  stmf_status st = check_samples_arg(c, V);
-  if (st != STMF_OK) return st;
-  if (!opts || !lambda || !A || !out) return set_error(c, STMF_EINVAL, "NULL argument");
-  if (d < 2 || d > 8) return set_error(c, STMF_EINVAL, "d must be in [2, 8]");
-  if (r < 1 || r > 64) return set_error(c, STMF_EINVAL, "r must be in [1, 64]");
-  if (opts->m < 1 || opts->m > 64 || opts->max_ls < 1 || opts->chunk < 1 ||
-      opts->max_evals < 1 || opts->max_iters < 0 || !(opts->pgtol >= 0.0) || !(opts->factr >= 0.0))
-    return set_error(c, STMF_EINVAL, "invalid optimiser options");
+  if (!V || !opts || !lambda || !A || !out) return set_error(c, STMF_EINVAL, "NULL argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const long long D = r + V->n * r;
-  // workspaces: the evaluation's, then the optimiser state
-  st = ensure_workspace(c, fg_workspace_bytes(c, V, r));
+  FitRun run;
+  stmf_status st = run.begin(c, V, nu, d, r, opts, lambda, A, s);
   if (st != STMF_OK) return st;
-  const size_t need = fit_bytes(D, opts->m);
-  if (need > c->fit_ws_bytes) {
-    if (cudaDeviceSynchronize() != cudaSuccess) return set_error(c, STMF_ECUDA, "sync");
-    if (c->fit_ws) cudaFree(c->fit_ws);
-    c->fit_ws = nullptr;
-    c->fit_ws_bytes = 0;
-    if (cudaMalloc(&c->fit_ws, need) != cudaSuccess)
-      return set_error(c, STMF_ENOMEM, "cudaMalloc of the optimiser state failed");
-    c->fit_ws_bytes = need;
-  }
-  FitLayout L = layout(c->fit_ws, D, opts->m);
-  fit_init<<<32, 256, 0, s>>>(L, lambda, A, (int)r, D);
-  if (cudaGetLastError() != cudaSuccess) return set_error(c, STMF_ECUDA, "fit_init launch");
-  if (opts->alpha_mode) {
-    st = stmf_norm_x(c, V, nu, d, &L.st->alpha, stream);
-    if (st != STMF_OK) return st;
-  }
-  StepOpts so;
-  so.pgtol = opts->pgtol;
-  so.factr = opts->factr;
-  so.c1 = 1e-3;
-  so.c2 = 0.9;
-  so.max_iters = opts->max_iters;
-  so.max_evals = opts->max_evals;
-  so.max_ls = opts->max_ls;
-  const double* alpha = &L.st->alpha;
-  const int32_t* skip = &L.st->done;
   int32_t done = 0;
-  long long enqueued = 0;
   while (!done) {
-    for (int k = 0; k < opts->chunk; ++k) {
-      st = enqueue_fg(c, V, nu, d, r, L.xt, L.xt + r, alpha, &L.st->ft, L.gt, L.gt + r, skip, s);
-      if (st != STMF_OK) return st;
-      lbfgs_step<<<1, LT, 0, s>>>(L, so);
-      if (cudaGetLastError() != cudaSuccess) return set_error(c, STMF_ECUDA, "lbfgs_step launch");
-    }
-    enqueued += opts->chunk;
-    if (cudaMemcpyAsync(&done, &L.st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return set_error(c, STMF_ECUDA, "reading the done flag");
-    if (!done && enqueued > opts->max_evals + opts->chunk)
+    st = run.enqueue_chunk(&done);
+    if (st != STMF_OK) return st;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return set_error(c, STMF_ECUDA, "sync");
+    if (!done && run.exhausted())
       return set_error(c, STMF_ECUDA, "optimiser did not stop within its evaluation budget");
   }
-  fit_export<<<32, 256, 0, s>>>(L, lambda, A, (int)r, D);
-  FitState h;
-  if (cudaMemcpyAsync(&h, L.st, sizeof(FitState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return set_error(c, STMF_ECUDA, "reading the optimiser state");
+  alignas(16) unsigned char hstate[512];
+  st = run.finish(hstate);
+  if (st != STMF_OK) return st;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return set_error(c, STMF_ECUDA, "sync");
   int32_t dev_status = 0;
   cudaMemcpy(&dev_status, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
-  out->f = h.f;
-  out->alpha = h.alpha;
-  out->g_inf = h.g_inf;
-  out->iters = h.iters;
-  out->evals = h.evals;
-  out->stop_reason = h.stop;
-  out->status = dev_status;
+  FitRun::result_from(hstate, dev_status, out);
   return STMF_OK;
 }
+

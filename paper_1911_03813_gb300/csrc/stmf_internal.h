@@ -110,6 +110,35 @@ stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int
                        const double* lambda, const double* A, const double* alpha, double* f,
                        double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s);
 size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
+
+// Bytes of the device optimiser state for D unknowns and m pairs.
+size_t fit_state_bytes(long long D, int m);
+
+// One run of the on-device L-BFGS (lbfgs.cu), driven asynchronously: begin() enqueues the set-up
+// (and alpha when asked), enqueue_chunk() enqueues opts.chunk evaluations + steps and an async
+// copy of the done flag to *done_host, finish() enqueues the export of the iterate into the
+// (lambda, A) buffers given to begin() and an async copy of the optimiser state to state_host
+// (FitRun::state_size() bytes), from which result_from() fills a stmf_fit_result.
+struct FitRun {
+  stmf_ctx* ctx = nullptr;
+  stmf_samples V{};
+  const double* nu = nullptr;
+  int d = 0;
+  int64_t r = 0;
+  stmf_fit_opts opts{};
+  double* lam_out = nullptr;
+  double* A_out = nullptr;
+  cudaStream_t stream = nullptr;
+  long long D = 0;
+  long long enqueued = 0;
+  stmf_status begin(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
+                    const stmf_fit_opts* opts, double* lambda, double* A, cudaStream_t s);
+  stmf_status enqueue_chunk(int32_t* done_host);
+  bool exhausted() const;
+  stmf_status finish(void* state_host);
+  static size_t state_size();
+  static void result_from(const void* state_host, int32_t dev_status, stmf_fit_result* out);
+};
 }  // namespace stmf
 
 // Record a device-side error in the status word: the first error wins.

@@ -347,3 +347,132 @@ def fit(V, nu, d, lam, A, opts=None, stream=None, ctx=None, **kw):
     return dict(f=res.f, alpha=res.alpha, g_inf=res.g_inf, iters=res.iters, evals=res.evals,
                 stop=res.stop_reason, stop_name=STOP_REASONS.get(res.stop_reason, "?"),
                 status=res.status)
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_fits", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("r_max", ctypes.c_int32), ("m_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_budget", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("V", Samples), ("V_on_host", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("r", ctypes.c_int64), ("n_starts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("nu", ctypes.c_void_p), ("x0", ctypes.c_void_p), ("lambda_out", ctypes.c_void_p),
+                ("A_out", ctypes.c_void_p), ("opts", FitOpts)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("best_start", ctypes.c_int32), ("best", FitResult),
+                ("total_evals", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("active_fits", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes_in_use", ctypes.c_size_t), ("slot_bytes", ctypes.c_size_t),
+                ("now", ctypes.c_double)]
+
+
+def _declare_server(L):
+    vp = ctypes.c_void_p
+    L.stmf_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.stmf_server_destroy.argtypes = [vp]
+    L.stmf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.stmf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(RequestResult), ctypes.c_int32]
+    L.stmf_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.stmf_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    for name in ("stmf_server_create", "stmf_server_destroy", "stmf_submit", "stmf_poll",
+                 "stmf_cancel", "stmf_server_get_stats"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_server)
+
+
+class Server:
+    """Continuously batched fits (stmf_server_*). Requests carry samples in host memory (numpy
+    storage arrays, copied to the device at admission) or on the device (torch tensors)."""
+
+    def __init__(self, device=0, max_fits=16, n_max=128, r_max=16, m_max=5, mem_budget=8 << 30):
+        cfg = ServerConfig(int(device), int(max_fits), int(n_max), int(r_max), int(m_max), 0,
+                           int(mem_budget))
+        h = ctypes.c_void_p()
+        st = lib().stmf_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise StmfError(st, "stmf_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, V, d, x0, nu=None, lam_out=None, A_out=None, opts=None, **kw):
+        """V: dict with host 'data' (numpy p x ld), optional 'scale', 'n', 'dtype' name; or a
+        device storage dict (torch). x0: host float64 array (n_starts, r + n r), each
+        [lambda; A column-major]. Returns a ticket."""
+        import numpy as np
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        if x0.ndim == 1:
+            x0 = x0[None, :]
+        data = V["data"]
+        on_host = not (hasattr(data, "is_cuda") and data.is_cuda)
+        if on_host:
+            arr = np.ascontiguousarray(data)
+            scale = V.get("scale")
+            if scale is not None:
+                scale = np.ascontiguousarray(scale, dtype=np.float32)
+            desc = Samples(arr.ctypes.data, scale.ctypes.data if scale is not None else None,
+                           int(V["n"]), int(arr.shape[0]), int(arr.shape[1]),
+                           _NAME_DTYPE[V["dtype"]], 0)
+            keep = (arr, scale)
+        else:
+            desc, keep = as_samples(V)
+        n = desc.n
+        r = (x0.shape[1]) // (n + 1)
+        o = opts if opts is not None else fit_options(**kw)
+        req = Request(desc, 1 if on_host else 0, int(d), int(r), int(x0.shape[0]), 0, _ptr(nu),
+                      x0.ctypes.data, _ptr(lam_out), _ptr(A_out), o)
+        t = ctypes.c_uint64()
+        st = lib().stmf_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if st != 0:
+            raise StmfError(st, "stmf_submit")
+        self._keep[t.value] = (keep, nu, lam_out, A_out)
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        res = RequestResult()
+        st = lib().stmf_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(res),
+                             int(timeout_ms))
+        if st == 6:
+            return None
+        if st != 0:
+            raise StmfError(st, "stmf_poll")
+        self._keep.pop(ticket, None)
+        b = res.best
+        return dict(state=res.state, best_start=res.best_start, f=b.f, alpha=b.alpha,
+                    g_inf=b.g_inf, iters=b.iters, evals=b.evals, stop=b.stop_reason,
+                    status=b.status, total_evals=res.total_evals, t_submit=res.t_submit,
+                    t_admit=res.t_admit, t_done=res.t_done, footprint=res.footprint)
+
+    def cancel(self, ticket):
+        st = lib().stmf_cancel(self.handle, ctypes.c_uint64(ticket))
+        if st != 0:
+            raise StmfError(st, "stmf_cancel")
+
+    def stats(self):
+        s = ServerStats()
+        lib().stmf_server_get_stats(self.handle, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().stmf_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
