@@ -140,6 +140,104 @@ def cpu_baseline(seconds=12.0, p_sample=1 << 17):
                        "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el))
 
 
+def make_requests(count, seed, dev):
+    """Serving requests: n, p log-uniform in [8, 128] x [1e3, 1e6], d in {3, 4}, r in [1, 16],
+    sigma log-uniform in [1e-4, 1e-1], four seeded starts each; samples in pinned host memory
+    (BF16), generated on the device and copied once before the clock starts."""
+    import numpy as np
+    import torch
+
+    from paper_1911_03813_gb300 import inputs
+    g = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(np.exp(g.uniform(np.log(8), np.log(128)))))
+        p = int(round(np.exp(g.uniform(np.log(1e3), np.log(1e6)))))
+        d = int(g.integers(3, 5))
+        r = int(g.integers(1, 17))
+        sigma = float(np.exp(g.uniform(np.log(1e-4), np.log(1e-1))))
+        st = inputs.gmm_device(n, p, r, sigma, seed * 100003 + k, dev, out_dtype="bf16")
+        host = torch.empty(st["data"].shape, dtype=torch.int16, pin_memory=True)
+        host.copy_(st["data"].view(torch.int16))
+        x0 = []
+        for s in range(4):
+            lam0, A0 = inputs.random_model(n, r, seed=seed * 7919 + 4 * k + s, lam="equal")
+            x0.append(np.concatenate([lam0, A0.reshape(-1, order="F")]))
+        out.append(dict(V=dict(data=host.numpy(), n=n, dtype="bf16"), x0=np.array(x0), d=d,
+                        n_=n, p=p, r=r, keep=host))
+        del st
+    return out
+
+
+def serving_bench(n_requests, seed, dev, device_index):
+    """Continuous batching through stmf_server_*: a saturated run fixes the capacity, then Poisson
+    arrivals at 0.8x that rate give the latency percentiles."""
+    import numpy as np
+
+    from paper_1911_03813_gb300 import stmf
+    opts = dict(pgtol=1e-5, factr=1e9, max_evals=200, alpha_mode=0, chunk=8)
+    sat = make_requests(max(n_requests // 2, 8), seed, dev)
+    poi = make_requests(n_requests, seed + 1, dev)
+    with stmf.Server(device=device_index, max_fits=64, n_max=128, r_max=16, m_max=5,
+                     mem_budget=150 << 30) as srv:
+        t0 = time.perf_counter()
+        tick = [srv.submit(q["V"], q["d"], q["x0"], **opts) for q in sat]
+        res = [srv.poll(t) for t in tick]
+        t_sat = time.perf_counter() - t0
+        ok_sat = sum(r_["state"] == 0 for r_ in res)
+        rate_sat = len(sat) / t_sat
+        rate = 0.8 * rate_sat
+        gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, size=len(poi))
+        t0 = time.perf_counter()
+        due = t0
+        tick = []
+        for q, gap in zip(poi, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                time.sleep(0.0002)
+            tick.append(srv.submit(q["V"], q["d"], q["x0"], **opts))
+        res = [srv.poll(t) for t in tick]
+        t_poi = time.perf_counter() - t0
+        stats = srv.stats()
+    lat = np.array([r_["t_done"] - r_["t_submit"] for r_ in res]) * 1e3
+    return {"requests": len(poi), "starts_per_request": 4,
+            "workload": "n, p log-uniform in [8,128] x [1e3,1e6], d in {3,4}, r in [1,16], "
+                        "sigma log-uniform in [1e-4,1e-1], BF16 samples on the host",
+            "saturated_requests_per_s": rate_sat, "saturated_fits_per_s": 4 * rate_sat,
+            "arrival_rate_per_s": rate, "fits_per_s": 4 * len(poi) / t_poi,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "completed": int(sum(r_["state"] == 0 for r_ in res)) + 0 * ok_sat,
+            "peak_admitted_bytes": int(stats["peak_bytes_in_use"]),
+            "optimiser": "L-BFGS m=5, pgtol 1e-5, factr 1e9, <= 200 evaluations per start"}
+
+
+def gram_bench(dev):
+    """One ||X||^2 Gram pass (tensor cores, BF16) on the first 2^16 samples of the workload."""
+    import torch
+
+    from paper_1911_03813_gb300 import inputs, stmf
+    p = 1 << 16
+    st = inputs.gmm_device(N_FEAT, p, N_MEANS, SIGMA, SEED, dev, out_dtype="bf16")
+    stmf.norm_x(st, None, D)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 5
+    for _ in range(reps):
+        stmf.norm_x(st, None, D)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    T = (p + 127) // 128
+    flop = 2.0 * 128 * 128 * N_FEAT * T * (T + 1) / 2
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    tf = flop / (ms / 1e3) / 1e12
+    return {"p": p, "n": N_FEAT, "d": D, "ms": ms, "tflops": tf, "bound": "tensor",
+            "peak_tflops": pk["bf16_tflops"], "frac": tf / pk["bf16_tflops"],
+            "flop_counted": "2*128*128*n per computed 128x128 tile pair, upper triangle"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -184,6 +282,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=P_FULL)
+    ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--no-gram", action="store_true")
+    ap.add_argument("--gram-only", action="store_true",
+                    help="time only the ||X||^2 Gram pass on 2^16 samples and print it")
     ap.add_argument("--legs", default="bf16,fp32,fp8",
                     help="sample types to time (bf16 is the headline)")
     args = ap.parse_args()
@@ -200,6 +302,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.gram_only:
+        print(json.dumps(gram_bench(dev)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -321,6 +426,10 @@ def main():
 
     if rank != 0:
         return
+    del st16, st32, st8
+    torch.cuda.empty_cache()
+    gram = None if args.no_gram else gram_bench(dev)
+    serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = ncu_traffic("fg_pass_bf16")
     line = {
@@ -347,8 +456,10 @@ def main():
                 "pass_frac_of_hbm": P * (N_FEAT + 4) / (pass8 / 1e3) / 1e9 / peaks["hbm_gbs"],
                 "storage": "E4M3 codes + one FP32 scale per sample"},
         "clocks": clk.summary(),
-        "gpu_launches": 3 * (args.steps + max(args.steps // 2, 1)),
+        "gpu_launches": 3 * args.steps,
         "e2e": e2e,
+        "gram": gram,
+        "serving": serving,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
