@@ -286,6 +286,59 @@ stmf_status stmf_cancel(stmf_server_t srv, uint64_t ticket);
 /* Counters of the server (host struct). */
 stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats* out);
 
+/* ------------------------------------------------------------------------------------------
+ * Sec. 5: massive or online data.
+ * ------------------------------------------------------------------------------------------ */
+
+/*
+ * stmf_fg_sampled -- Alg. 2 on the stochastic Kruskal tensor of Lemma 5.1: the s rows
+ * idx[0..s) of V (drawn with replacement by the caller; a row may repeat) with weights 1/s, whose
+ * TTSVs X~ a^{d-1} are unbiased for X a^{d-1}. Arguments as for stmf_fg, plus
+ *  idx   device, s int64 row indices in [0, V->p); an index outside that range reads as a zero
+ *        sample and sets STMF_EINVAL in the device status word.
+ * Runs on the CUDA cores (the pass gathers its rows). Enqueued on `stream`; asynchronous.
+ */
+stmf_status stmf_fg_sampled(stmf_ctx_t ctx, const stmf_samples* V, const int64_t* idx, int64_t s,
+                            int32_t d, int64_t r, const double* lambda, const double* A,
+                            const double* alpha, double* f, double* g_lambda, double* G_A,
+                            stmf_stream_t stream);
+
+/* Adam (Kingma & Ba, 2015) with the schedule of Sec. 5 (paper values as defaults). */
+typedef struct {
+  double lr0;          /* initial learning rate (0.01) */
+  double lr1;          /* rate after the first non-decrease (0.001) */
+  double beta1, beta2, eps;   /* 0.9, 0.999, 1e-8 */
+  int64_t epoch;       /* iterations per epoch (100) */
+  int64_t max_epochs;  /* 0: no limit besides the index rows given */
+} stmf_adam_opts;
+
+typedef struct {
+  double f_est;        /* estimated shifted f at the returned iterate */
+  int64_t epochs;      /* epochs completed */
+  int64_t iters;       /* Adam steps in the returned state */
+  int32_t drops;       /* times the estimate did not decrease (2 = stopped) */
+  int32_t status;      /* device status word */
+} stmf_adam_result;
+
+stmf_status stmf_adam_default_opts(stmf_adam_opts* opts);
+
+/*
+ * stmf_adam -- Sec. 5's stochastic method: Adam on (lambda, A) with one sampled stochastic
+ * gradient per iteration (Lemma 5.1), an estimate of the shifted objective after every epoch on
+ * the fixed rows est_idx (Sec. 5 uses 1,000), the learning rate dropping to lr1 and the state
+ * returning to the prior epoch at the first non-decrease, and a stop (returning the prior epoch's
+ * iterate) at the second. Returning to the prior epoch restores the Adam moments and step count
+ * too (this library's reading). All state stays on the device; the host reads one flag per epoch.
+ *  sample_idx  device, iters x s int64: row t holds the s sampled rows of iteration t.
+ *  est_idx     device, est_s int64: the fixed estimation rows.
+ *  lambda, A   device; start on entry, final iterate on return.   out  host.
+ * Synchronous (work on `stream`). Runs at most floor(iters / epoch) epochs.
+ */
+stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d, int64_t r,
+                      const stmf_adam_opts* opts, const int64_t* sample_idx, int64_t iters,
+                      int64_t s, const int64_t* est_idx, int64_t est_s, double* lambda, double* A,
+                      stmf_adam_result* out, stmf_stream_t stream);
+
 /*
  * stmf_fg_noalloc -- the evaluation of stmf_fg for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface variant of stmf_fg (same kernels, same

@@ -127,8 +127,18 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
       const int s = e / n, i = e - s * n;
       TC v = (TC)0;
       if (s < valid) {
-        v = widen<TC>(V[(s0 + s) * ld + i]);
-        if (DT == STMF_E4M3) v *= (TC)prm.scale[s0 + s];
+        int64_t row = s0 + s;
+        if (prm.idx) {  // sampled rows (Sec. 5): a row outside the storage reads as zero
+          row = prm.idx[s0 + s];
+          if (row < 0 || row >= prm.rows) {
+            if (i == 0) stmf_set_status(prm.status, STMF_EINVAL);
+            row = -1;
+          }
+        }
+        if (row >= 0) {
+          v = widen<TC>(V[row * ld + i]);
+          if (DT == STMF_E4M3) v *= (TC)prm.scale[row];
+        }
       }
       Vs[s * vst + i] = v;
     }

@@ -90,16 +90,27 @@ size_t stmf::fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_
   return fg_ws_bytes(plan_fg(c, V, r), r);
 }
 
-stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
+stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double* nu, int d, int64_t r,
                              const double* lambda, const double* A, const double* alpha, double* f,
-                             double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s) {
-  stmf_status st = check_samples(c, V);
+                             double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
+                             const int64_t* idx, int64_t n_idx) {
+  stmf_status st = check_samples(c, V_in);
   if (st != STMF_OK) return st;
+  if (idx && n_idx < 1) return fail(c, STMF_EINVAL, "the number of sampled rows must be >= 1");
+  // a sampled pass processes n_idx rows gathered through idx (the CUDA-core pass gathers)
+  stmf_samples Vs = *V_in;
+  if (idx) Vs.p = n_idx;
+  const stmf_samples* V = &Vs;
   if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
   if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
   if (!lambda || !A || !f || !g_lambda || !G_A) return fail(c, STMF_EINVAL, "NULL model or output pointer");
   const int n = (int)V->n;
-  const FgPlan pl = plan_fg(c, V, r);
+  FgPlan pl = plan_fg(c, V, r);
+  if (idx && pl.tc) {  // gathers take the CUDA-core pass
+    pl.tc = false;
+    pl.grid = stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
+    pl.partial_doubles = size_t(pl.grid) * pl.L;
+  }
   if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
     return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
   st = ensure_ws(c, fg_ws_bytes(pl, r));
@@ -123,6 +134,8 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* n
   prm.flush_tiles = 16;
   prm.status = c->status;
   prm.skip = skip;
+  prm.idx = idx;
+  prm.rows = V_in->p;
   cudaEvent_t ev_end = nullptr;
   if (c->profiling && c->ev_used + 2 <= 2 * 65536) {
     while (c->ev_pool.size() < c->ev_used + 2) {

@@ -24,6 +24,8 @@ struct FgParams {
   int flush_tiles;      // FP32 accumulators are folded into FP64 every flush_tiles tiles
   int32_t* status;      // device status word
   const int32_t* skip;  // when non-null and nonzero at launch, the kernel does nothing
+  const int64_t* idx;   // when non-null: sample k of the pass is row idx[k] of the storage
+  int64_t rows;         // rows of the storage (bounds of idx)
 };
 
 // Finalisation of Alg. 2 lines 3-9 from the reduced (w, Y).
@@ -108,7 +110,8 @@ stmf_status ensure_workspace(stmf_ctx* c, size_t bytes);
 // Enqueue one evaluation of Alg. 2 (fused pass + model terms) with optional skip flag.
 stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
                        const double* lambda, const double* A, const double* alpha, double* f,
-                       double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s);
+                       double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
+                       const int64_t* idx = nullptr, int64_t n_idx = 0);
 size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
 
 // Bytes of the device optimiser state for D unknowns and m pairs.

@@ -476,3 +476,73 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class AdamOpts(ctypes.Structure):
+    _fields_ = [("lr0", ctypes.c_double), ("lr1", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("epoch", ctypes.c_int64),
+                ("max_epochs", ctypes.c_int64)]
+
+
+class AdamResult(ctypes.Structure):
+    _fields_ = [("f_est", ctypes.c_double), ("epochs", ctypes.c_int64), ("iters", ctypes.c_int64),
+                ("drops", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+def _declare_stochastic(L):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.stmf_fg_sampled.argtypes = [vp, ctypes.POINTER(Samples), vp, i64, i32, i64, vp, vp, vp, vp,
+                                  vp, vp, vp]
+    L.stmf_adam_default_opts.argtypes = [ctypes.POINTER(AdamOpts)]
+    L.stmf_adam.argtypes = [vp, ctypes.POINTER(Samples), i32, i64, ctypes.POINTER(AdamOpts), vp,
+                            i64, i64, vp, i64, vp, vp, ctypes.POINTER(AdamResult), vp]
+    for name in ("stmf_fg_sampled", "stmf_adam_default_opts", "stmf_adam"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_stochastic)
+
+
+def _check_idx(idx, name):
+    if idx.dtype != torch.int64 or not idx.is_cuda or not idx.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA int64 tensor" % name)
+
+
+def fg_sampled(V, idx, d, lam, A, alpha=None, stream=None, ctx=None):
+    """stmf_fg_sampled: Alg. 2 on the rows idx of V with weights 1/len(idx) (Lemma 5.1)."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    _check_idx(idx, "idx")
+    n, r = desc.n, lam.shape[0]
+    f = torch.empty(1, dtype=torch.float64, device=lam.device)
+    gl = torch.empty(r, dtype=torch.float64, device=lam.device)
+    GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
+    st = lib().stmf_fg_sampled(ctx.handle, ctypes.byref(desc), _ptr(idx), int(idx.numel()),
+                               int(d), int(r), _ptr(lam), _ptr(A), _ptr(alpha), _ptr(f),
+                               _ptr(gl), _ptr(GA), _stream(stream))
+    ctx.check(st, "stmf_fg_sampled")
+    del keep
+    return f, gl, GA
+
+
+def adam(V, d, lam, A, sample_idx, est_idx, stream=None, ctx=None, **kw):
+    """stmf_adam: Sec. 5's Adam schedule; sample_idx (iters, s) and est_idx (e,) CUDA int64.
+    lam, A (column-major) are updated in place. Returns a dict."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    _check_idx(sample_idx, "sample_idx")
+    _check_idx(est_idx, "est_idx")
+    o = AdamOpts()
+    lib().stmf_adam_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    res = AdamResult()
+    iters, s = sample_idx.shape
+    st = lib().stmf_adam(ctx.handle, ctypes.byref(desc), int(d), int(lam.shape[0]),
+                         ctypes.byref(o), _ptr(sample_idx), int(iters), int(s), _ptr(est_idx),
+                         int(est_idx.numel()), _ptr(lam), _ptr(A), ctypes.byref(res),
+                         _stream(stream))
+    ctx.check(st, "stmf_adam")
+    del keep
+    return dict(f_est=res.f_est, epochs=res.epochs, iters=res.iters, drops=res.drops,
+                status=res.status)

@@ -1,0 +1,82 @@
+"""Sec. 5 on the device: sampled evaluation (Lemma 5.1) and the Adam schedule (-m gpu).
+
+The sampled rows are inputs shared by the device and the oracle."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import formats, stochastic  # noqa: E402
+from paper_1911_03813_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def stmf():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_03813_gb300 import stmf as s
+    torch.cuda.set_device(0)
+    return s
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("s", [1, 10, 100, 1000])
+def test_fg_sampled_parity(stmf, dtype, s):
+    n, p, r, d = 50, 20000, 6, 3
+    data = inputs.gmm(n, p, 6, 0.1, seed=s + 3)
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    bits = inputs.storage_bits(st)
+    Vd = formats.decode_bf16(bits) if dtype == "bf16" else np.asarray(bits, dtype=np.float64)
+    idx = np.random.default_rng(s).integers(0, p, size=s)
+    lam, A = inputs.random_model(n, r, seed=s)
+    f_ref, gl_ref, GA_ref = stochastic.fg_sampled(Vd.T, idx, lam, A, d)
+    f, gl, GA = stmf.fg_sampled(st, torch.tensor(idx, device="cuda"), d,
+                                torch.tensor(lam, device="cuda"),
+                                torch.tensor(A.T.copy(), device="cuda").T)
+    torch.cuda.synchronize()
+    assert stmf.default_context().device_status() == 0
+    scale = abs(f_ref) + 1e-300
+    assert abs(f.item() - f_ref) <= TOL[dtype] * max(scale, np.abs(gl_ref).max())
+    assert rel(gl.cpu().numpy(), gl_ref) <= TOL[dtype]
+    assert rel(GA.cpu().numpy(), GA_ref) <= TOL[dtype]
+
+
+def test_fg_sampled_out_of_range_index_is_reported(stmf):
+    st = inputs.to_storage(np.ones((100, 8)), "f32", device="cuda")
+    idx = torch.tensor([0, 5, 100], device="cuda")   # 100 is outside [0, p)
+    stmf.fg_sampled(st, idx, 3, torch.ones(2, dtype=torch.float64, device="cuda"),
+                    torch.ones((2, 8), dtype=torch.float64, device="cuda").T)
+    assert stmf.default_context().device_status() == 1   # STMF_EINVAL
+
+
+def test_adam_matches_oracle_schedule(stmf):
+    """FP64 samples: the device Adam takes the oracle's steps (same sampled rows), through the
+    learning-rate drop and the stop."""
+    n, p, r, d = 20, 5000, 3, 3
+    data = inputs.gmm(n, p, r, 0.1, seed=41, weights="equal")
+    st = inputs.to_storage(data["V"], "f64", device="cuda")
+    V = data["V"].T
+    lam0, A0 = inputs.random_model(n, r, seed=42, lam="equal")
+    g = np.random.default_rng(43)
+    sample_idx = g.integers(0, p, size=(3000, 50))
+    est_idx = g.integers(0, p, size=500)
+    ref = stochastic.adam(V, lam0, A0, d, sample_idx, est_idx, epoch=20)
+    lam = torch.tensor(lam0, device="cuda")
+    A = torch.tensor(A0.T.copy(), device="cuda").T
+    out = stmf.adam(st, d, lam, A, torch.tensor(sample_idx, device="cuda"),
+                    torch.tensor(est_idx, device="cuda"), epoch=20)
+    assert out["status"] == 0
+    assert out["epochs"] == ref["epochs"]
+    assert out["f_est"] == pytest.approx(ref["f_est"], rel=1e-9, abs=1e-14)
+    x = np.concatenate([lam.cpu().numpy(), A.cpu().numpy().reshape(-1, order="F")])
+    xr = np.concatenate([ref["lam"], ref["A"].reshape(-1, order="F")])
+    assert rel(x, xr) < 1e-8
