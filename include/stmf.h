@@ -41,6 +41,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define STMF_API __attribute__((visibility("default")))
+#else
+#define STMF_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -81,30 +87,30 @@ typedef struct {
 typedef struct stmf_ctx* stmf_ctx_t;
 
 /* Library version, as 10000*major + 100*minor + patch. */
-int stmf_version(void);
+STMF_API int stmf_version(void);
 
 /* Human-readable name of a status code (static storage). */
-const char* stmf_status_string(int status);
+STMF_API const char* stmf_status_string(int status);
 
 /* Create a context on CUDA device `device`. Fails with STMF_EUNSUPPORTED when the device is
  * not compute capability 10.3 (the kernels are built for sm_103a only). *out is set on
  * success. */
-stmf_status stmf_create(int device, stmf_ctx_t* out);
+STMF_API stmf_status stmf_create(int device, stmf_ctx_t* out);
 
 /* Destroy a context and free its workspace. Synchronises the device. NULL is accepted. */
-stmf_status stmf_destroy(stmf_ctx_t ctx);
+STMF_API stmf_status stmf_destroy(stmf_ctx_t ctx);
 
 /* Text describing the last error returned on this context (static per context; valid until
  * the next call on it). */
-const char* stmf_last_error(stmf_ctx_t ctx);
+STMF_API const char* stmf_last_error(stmf_ctx_t ctx);
 
 /* Grow the workspace so that stmf_fg / stmf_norm_x on V with rank r need no allocation.
  * Synchronises the device when it allocates. */
-stmf_status stmf_reserve(stmf_ctx_t ctx, const stmf_samples* V, int64_t r);
+STMF_API stmf_status stmf_reserve(stmf_ctx_t ctx, const stmf_samples* V, int64_t r);
 
 /* Read the device status word (STMF_OK or the first device-side error since the last read),
  * waiting for `stream`, and reset it to STMF_OK. *out_host is a host pointer. */
-stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, int32_t* out_host);
+STMF_API stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, int32_t* out_host);
 
 /*
  * stmf_fg -- function value and gradient by Alg. 2 (fg_implicit, Sec. 3.4):
@@ -129,7 +135,7 @@ stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, int32_t* ou
  *  f        device, 1 FP64 (out).   g_lambda  device, r FP64 (out).   G_A  device, n x r (out).
  * Outputs may not alias inputs. Enqueued on `stream`; asynchronous.
  */
-stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+STMF_API stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
                     int64_t r, const double* lambda, const double* A, const double* alpha,
                     double* f, double* g_lambda, double* G_A, stmf_stream_t stream);
 
@@ -140,7 +146,7 @@ stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int
  *  V, nu, d   as for stmf_fg.     alpha_out  device, 1 FP64 (out).
  * Enqueued on `stream`; asynchronous.
  */
-stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+STMF_API stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
                         double* alpha_out, stmf_stream_t stream);
 
 /*
@@ -149,8 +155,8 @@ stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu,
  * waits for the recorded events, returns the summed pass time in milliseconds and the number of
  * passes (host pointers), and clears the record. At most 65536 passes are recorded.
  */
-stmf_status stmf_profile_enable(stmf_ctx_t ctx, int32_t enable);
-stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* count_host);
+STMF_API stmf_status stmf_profile_enable(stmf_ctx_t ctx, int32_t enable);
+STMF_API stmf_status stmf_profile_read(stmf_ctx_t ctx, double* total_ms_host, int64_t* count_host);
 
 /*
  * Optimiser options of stmf_fit. The paper (Sec. 4) runs L-BFGS-B without bounds, memory m = 5,
@@ -185,7 +191,7 @@ typedef struct {
 } stmf_fit_result;
 
 /* Fill *opts with the defaults listed above (pgtol = 1e-5). */
-stmf_status stmf_fit_default_opts(stmf_fit_opts* opts);
+STMF_API stmf_status stmf_fit_default_opts(stmf_fit_opts* opts);
 
 /*
  * stmf_fit -- minimise f(lambda, A) = ||X - M||^2 (eq. optFunc) from the start (lambda, A) with
@@ -199,7 +205,7 @@ stmf_status stmf_fit_default_opts(stmf_fit_opts* opts);
  *  out           host; the result.
  * Synchronous: returns when the optimiser has stopped (work is issued on `stream`).
  */
-stmf_status stmf_fit(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
+STMF_API stmf_status stmf_fit(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
                      int64_t r, const stmf_fit_opts* opts, double* lambda, double* A,
                      stmf_fit_result* out, stmf_stream_t stream);
 
@@ -262,29 +268,43 @@ typedef struct {
 
 /* Create a server: allocates max_fits slots (fails with STMF_ENOMEM when they alone exceed
  * mem_budget) and starts the scheduler thread. */
-stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_server_t* out);
+STMF_API stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_server_t* out);
 
 /* Stop the scheduler (running requests are cancelled), free everything. */
-stmf_status stmf_server_destroy(stmf_server_t srv);
+STMF_API stmf_status stmf_server_destroy(stmf_server_t srv);
 
 /* Queue a request. The struct and the start points x0 are copied at submission; samples given
  * in host memory (V_on_host = 1) are copied to the device at admission, so they (and device
  * samples, nu and the output buffers) must stay valid until the request has finished.
  * *ticket identifies the request. STMF_EINVAL for invalid arguments; STMF_ENOMEM when its
  * footprint alone exceeds what the budget leaves after the slots. */
-stmf_status stmf_submit(stmf_server_t srv, const stmf_request* req, uint64_t* ticket);
+STMF_API stmf_status stmf_submit(stmf_server_t srv, const stmf_request* req, uint64_t* ticket);
 
 /* Wait up to timeout_ms (0: do not wait, < 0: no limit) for the request; fills *out (host) and
  * returns STMF_OK once it has finished (successfully or not: see out->state), STMF_ENOTREADY
  * while it is queued or running, STMF_EINVAL for an unknown ticket. */
-stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_request_result* out,
+STMF_API stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_request_result* out,
                       int32_t timeout_ms);
 
 /* Cancel a queued or running request; it finishes with state STMF_ECANCELLED. */
-stmf_status stmf_cancel(stmf_server_t srv, uint64_t ticket);
+STMF_API stmf_status stmf_cancel(stmf_server_t srv, uint64_t ticket);
 
 /* Counters of the server (host struct). */
-stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats* out);
+STMF_API stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats* out);
+
+/*
+ * stmf_rrf_start -- the randomized-range-finder start of eq. rrf (Sec. 4.2): A0 = V Omega with
+ * unit-norm columns, Omega a p x r_hat Gaussian test matrix. Omega is never stored: entry (l, j)
+ * is drawn inside the pass from Philox4x32-10 (Salmon et al., SC 2011) with counter
+ * (l mod 2^32, l div 2^32, j, 0) and key (seed mod 2^32, seed div 2^32); the first two output
+ * words give u1, u2 = (x + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). The
+ * sums are FP64.
+ *  V        samples (any type).     r_hat  1..64 columns (n * r_hat limited by shared memory).
+ *  seed     key of the generator.   A0     device, n x r_hat FP64 column-major (out).
+ * Enqueued on `stream`; asynchronous.
+ */
+STMF_API stmf_status stmf_rrf_start(stmf_ctx_t ctx, const stmf_samples* V, int64_t r_hat, uint64_t seed,
+                           double* A0, stmf_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Sec. 5: massive or online data.
@@ -298,7 +318,7 @@ stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats* out);
  *        sample and sets STMF_EINVAL in the device status word.
  * Runs on the CUDA cores (the pass gathers its rows). Enqueued on `stream`; asynchronous.
  */
-stmf_status stmf_fg_sampled(stmf_ctx_t ctx, const stmf_samples* V, const int64_t* idx, int64_t s,
+STMF_API stmf_status stmf_fg_sampled(stmf_ctx_t ctx, const stmf_samples* V, const int64_t* idx, int64_t s,
                             int32_t d, int64_t r, const double* lambda, const double* A,
                             const double* alpha, double* f, double* g_lambda, double* G_A,
                             stmf_stream_t stream);
@@ -320,7 +340,7 @@ typedef struct {
   int32_t status;      /* device status word */
 } stmf_adam_result;
 
-stmf_status stmf_adam_default_opts(stmf_adam_opts* opts);
+STMF_API stmf_status stmf_adam_default_opts(stmf_adam_opts* opts);
 
 /*
  * stmf_adam -- Sec. 5's stochastic method: Adam on (lambda, A) with one sampled stochastic
@@ -334,7 +354,7 @@ stmf_status stmf_adam_default_opts(stmf_adam_opts* opts);
  *  lambda, A   device; start on entry, final iterate on return.   out  host.
  * Synchronous (work on `stream`). Runs at most floor(iters / epoch) epochs.
  */
-stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d, int64_t r,
+STMF_API stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d, int64_t r,
                       const stmf_adam_opts* opts, const int64_t* sample_idx, int64_t iters,
                       int64_t s, const int64_t* est_idx, int64_t est_s, double* lambda, double* A,
                       stmf_adam_result* out, stmf_stream_t stream);
@@ -368,7 +388,7 @@ stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d, int64_t 
  *           to a word inside the scratch that the call clears first.
  * Enqueued on `stream`; asynchronous; the current device must be the device of all pointers.
  */
-stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, int32_t d, int64_t r,
+STMF_API stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, int32_t d, int64_t r,
                             const double* lambda, const double* A, const double* alpha,
                             double* f, double* g_lambda, double* G_A, int32_t* status,
                             stmf_stream_t stream);

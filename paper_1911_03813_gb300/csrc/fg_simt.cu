@@ -62,7 +62,34 @@ size_t smem_bytes(int n, int rp) {
   return b;
 }
 
-template <typename TC, int DT, int JB>
+// Philox4x32-10 (Salmon et al., SC 2011) and a Box-Muller normal: entry (l, j) of the test matrix
+// of eq. rrf uses counter (l mod 2^32, l div 2^32, j, 0) and key (seed mod 2^32, seed div 2^32);
+// words x0, x1 give u_k = (x_k + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ double rrf_omega(int64_t l, int j, uint64_t seed) {
+  uint32_t c0 = (uint32_t)(uint64_t)l, c1 = (uint32_t)((uint64_t)l >> 32), c2 = (uint32_t)j, c3 = 0;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int rnd = 0; rnd < 10; ++rnd) {
+    if (rnd > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  const double u1 = ((double)c0 + 0.5) * 0x1p-32;
+  const double u2 = ((double)c1 + 0.5) * 0x1p-32;
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// RRF = false: the fused pass of Alg. 2. RRF = true: the randomized range finder of eq. rrf,
+// Y_part = sum_l v_l omega_l^T with the test matrix drawn in phase 1 (no w).
+template <typename TC, int DT, int JB, bool RRF = false>
 __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
   using TS_t = typename Storage<DT>::T;
   if (prm.skip && *prm.skip) return;
@@ -87,9 +114,11 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
   double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
 
   // A (FP64, n x r column-major) -> As[i][j] in the compute type, zero-padded to rp columns.
-  for (int e = tid; e < n * rp; e += NT) {
-    const int i = e / rp, j = e - i * rp;
-    As[e] = j < r ? (TC)prm.A[i + size_t(n) * j] : (TC)0;
+  if constexpr (!RRF) {
+    for (int e = tid; e < n * rp; e += NT) {
+      const int i = e / rp, j = e - i * rp;
+      As[e] = j < r ? (TC)prm.A[i + size_t(n) * j] : (TC)0;
+    }
   }
   for (int e = tid; e < (NT / 32) * 16; e += NT) wsh[e] = 0.0;
 
@@ -146,6 +175,13 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
       nus[tid] = tid < valid ? (TC)(prm.nu ? prm.nu[s0 + tid] : prm.nu_uniform) : (TC)0;
     __syncthreads();
 
+    if constexpr (RRF) {
+      // phase 1 (range finder): W = the rows of the Gaussian test matrix for these samples
+      for (int e = tid; e < TS * rp; e += NT) {
+        const int s = e / rp, j = e - (e / rp) * rp;
+        Ws[e] = (s < valid && j < r) ? (TC)rrf_omega(s0 + s, j, prm.seed) : (TC)0;
+      }
+    } else
     // phase 1: z = v_s^T a_j for the thread's sample s and column quads q0, q0+4, ...
     {
       const int s = tid % TS;
@@ -230,25 +266,25 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
   }
 }
 
-template <typename TC, int DT, int JB>
+template <typename TC, int DT, int JB, bool RRF = false>
 cudaError_t launch_one(const FgParams& prm, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<TC>(prm.n, prm.r_pad);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB>,
+    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB, RRF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_simt_kernel<TC, DT, JB><<<grid, NT, smem, s>>>(prm);
+  fg_simt_kernel<TC, DT, JB, RRF><<<grid, NT, smem, s>>>(prm);
   return cudaGetLastError();
 }
 
-template <typename TC, int DT>
+template <typename TC, int DT, bool RRF = false>
 cudaError_t launch_jb(const FgParams& prm, int grid, cudaStream_t s) {
-  if (prm.r_pad % 16 == 0) return launch_one<TC, DT, 16>(prm, grid, s);
-  if (prm.r_pad % 8 == 0) return launch_one<TC, DT, 8>(prm, grid, s);
-  return launch_one<TC, DT, 4>(prm, grid, s);
+  if (prm.r_pad % 16 == 0) return launch_one<TC, DT, 16, RRF>(prm, grid, s);
+  if (prm.r_pad % 8 == 0) return launch_one<TC, DT, 8, RRF>(prm, grid, s);
+  return launch_one<TC, DT, 4, RRF>(prm, grid, s);
 }
 
 }  // namespace
@@ -277,6 +313,20 @@ cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_
     case STMF_F32: return launch_jb<float, STMF_F32>(prm, grid, s);
     case STMF_BF16: return launch_jb<float, STMF_BF16>(prm, grid, s);
     case STMF_E4M3: return launch_jb<float, STMF_E4M3>(prm, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int rrf_grid(int, int n, int r, int64_t p, int num_sms) {
+  return fg_simt_grid(STMF_F64, n, r, p, num_sms);  // the range finder accumulates in FP64
+}
+
+cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  switch (dtype) {
+    case STMF_F64: return launch_jb<double, STMF_F64, true>(prm, grid, s);
+    case STMF_F32: return launch_jb<double, STMF_F32, true>(prm, grid, s);
+    case STMF_BF16: return launch_jb<double, STMF_BF16, true>(prm, grid, s);
+    case STMF_E4M3: return launch_jb<double, STMF_E4M3, true>(prm, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -136,6 +136,14 @@ cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s) {
+  const int L = prm.r + prm.n * prm.r;
+  const int nb = (L + RE - 1) / RE;
+  if (prm.grid > RY * RMAX) return cudaErrorInvalidValue;
+  reduce_kernel<<<nb, RE * RY, 0, s>>>(prm, L, nb);
+  return cudaGetLastError();
+}
+
 cudaError_t reduce_scalar_launch(const double* partials, int count, double* out,
                                  int32_t* status, cudaStream_t s) {
   reduce_scalar_kernel<<<1, 32, 0, s>>>(partials, count, out, status);

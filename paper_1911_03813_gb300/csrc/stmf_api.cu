@@ -268,6 +268,65 @@ stmf_status stmf_fg(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32
                           reinterpret_cast<cudaStream_t>(stream));
 }
 
+namespace {
+__global__ void normalize_columns(const double* Y, int n, int r, double* A0) {
+  // one warp per column: A0[:, j] = Y[:, j] / ||Y[:, j]||_2 (lanes stride the rows, fixed order)
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (j >= r) return;
+  double ss = 0.0;
+  for (int i = lane; i < n; i += 32) ss += Y[i + size_t(n) * j] * Y[i + size_t(n) * j];
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const double inv = 1.0 / sqrt(ss);
+  for (int i = lane; i < n; i += 32) A0[i + size_t(n) * j] = Y[i + size_t(n) * j] * inv;
+}
+}  // namespace
+
+stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, uint64_t seed,
+                           double* A0, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  stmf_status st = check_samples(c, V);
+  if (st != STMF_OK) return st;
+  if (r_hat < 1 || r_hat > 64) return fail(c, STMF_EINVAL, "r_hat must be in [1, 64]");
+  if (!A0) return fail(c, STMF_EINVAL, "A0 is NULL");
+  const int n = (int)V->n;
+  if (stmf::fg_simt_smem(STMF_F64, n, (int)r_hat) > kMaxSmem)
+    return fail(c, STMF_EINVAL, "n * r_hat too large for the range finder (shared memory)");
+  const int grid = stmf::rrf_grid(V->dtype, n, (int)r_hat, V->p, c->num_sms);
+  const size_t L = size_t(r_hat) + size_t(n) * size_t(r_hat);
+  st = ensure_ws(c, (size_t(grid) * L + L) * sizeof(double));
+  if (st != STMF_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* partials = static_cast<double*>(c->ws);
+  double* yw = partials + size_t(grid) * L;
+  stmf::FgParams prm{};
+  prm.V = V->data;
+  prm.scale = V->scale;
+  prm.partials = partials;
+  prm.p = V->p;
+  prm.n = n;
+  prm.ld = (int)V->ld;
+  prm.d = 2;
+  prm.r = (int)r_hat;
+  prm.r_pad = (int)((r_hat + 3) / 4 * 4);
+  prm.flush_tiles = 1 << 30;  // FP64 accumulators: no intermediate folds needed
+  prm.status = c->status;
+  prm.seed = seed;
+  cudaError_t e = stmf::rrf_launch(V->dtype, prm, grid, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "range finder launch");
+  stmf::ModelParams mp{};
+  mp.partials = partials;
+  mp.grid = grid;
+  mp.yw = yw;
+  mp.n = n;
+  mp.r = (int)r_hat;
+  e = stmf::reduce_partials_launch(mp, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "range finder reduction launch");
+  normalize_columns<<<(int)((r_hat + 7) / 8), 256, 0, s>>>(yw + r_hat, n, (int)r_hat, A0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "normalisation launch");
+  return STMF_OK;
+}
+
 stmf_status stmf_profile_enable(stmf_ctx_t c, int32_t enable) {
   if (!c) return STMF_EINVAL;
   c->profiling = enable != 0;

@@ -26,6 +26,7 @@ struct FgParams {
   const int32_t* skip;  // when non-null and nonzero at launch, the kernel does nothing
   const int64_t* idx;   // when non-null: sample k of the pass is row idx[k] of the storage
   int64_t rows;         // rows of the storage (bounds of idx)
+  uint64_t seed;        // randomized range finder: key of the Philox test matrix
 };
 
 // Finalisation of Alg. 2 lines 3-9 from the reduced (w, Y).
@@ -61,6 +62,11 @@ struct GramParams {
 size_t fg_simt_smem(int dtype, int n, int r);  // dynamic shared memory of the pass
 int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+// Randomized range finder (eq. rrf): block partials of V Omega into prm.partials (w part zero).
+int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms);
+cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+// Sum the block partials only (no model terms): yw = sum_g partials[g].
+cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);

@@ -546,3 +546,26 @@ def adam(V, d, lam, A, sample_idx, est_idx, stream=None, ctx=None, **kw):
     del keep
     return dict(f_est=res.f_est, epochs=res.epochs, iters=res.iters, drops=res.drops,
                 status=res.status)
+
+
+def _declare_rrf(L):
+    L.stmf_rrf_start.argtypes = [ctypes.c_void_p, ctypes.POINTER(Samples), ctypes.c_int64,
+                                 ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    L.stmf_rrf_start.restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_rrf)
+
+
+def rrf_start(V, r_hat, seed, stream=None, ctx=None):
+    """stmf_rrf_start: A0 = V Omega with unit-norm columns (eq. rrf), Omega drawn on the device
+    from Philox4x32-10. Returns A0 as an (n, r_hat) column-major CUDA float64 view."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    A0 = torch.empty((int(r_hat), desc.n), dtype=torch.float64,
+                     device=torch.device("cuda", ctx.device)).T
+    st = lib().stmf_rrf_start(ctx.handle, ctypes.byref(desc), int(r_hat), ctypes.c_uint64(seed),
+                              _ptr(A0), _stream(stream))
+    ctx.check(st, "stmf_rrf_start")
+    del keep
+    return A0

@@ -80,3 +80,26 @@ def test_adam_matches_oracle_schedule(stmf):
     x = np.concatenate([lam.cpu().numpy(), A.cpu().numpy().reshape(-1, order="F")])
     xr = np.concatenate([ref["lam"], ref["A"].reshape(-1, order="F")])
     assert rel(x, xr) < 1e-8
+
+
+@pytest.mark.parametrize("dtype,n,p,r_hat", [("f64", 30, 7000, 5), ("f32", 100, 20000, 10),
+                                             ("bf16", 256, 9000, 16), ("e4m3", 64, 3000, 3)])
+def test_rrf_start_parity(stmf, dtype, n, p, r_hat):
+    """eq. rrf with the test matrix drawn on the device from Philox4x32-10 (same draws as the
+    oracle's generator)."""
+    from oracle import philox, rrf
+    data = inputs.gmm(n, p, 4, 0.1, seed=p)
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    bits = inputs.storage_bits(st)
+    if dtype == "bf16":
+        Vd = formats.decode_bf16(bits)
+    elif dtype == "e4m3":
+        Vd = formats.dequantize_e4m3(bits, st["scale"].cpu().numpy())
+    else:
+        Vd = np.asarray(bits, dtype=np.float64)
+    seed = 0x1234ABCD5678 + p
+    ref = rrf.rrf_start(Vd.T, philox.gaussian_test_matrix(p, r_hat, seed))
+    A0 = stmf.rrf_start(st, r_hat, seed).cpu().numpy()
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    assert rel(A0, ref) < tol, rel(A0, ref)
+    assert np.allclose(np.linalg.norm(A0, axis=0), 1.0, atol=1e-13)
