@@ -140,6 +140,28 @@ STMF_API stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double
                     double* f, double* g_lambda, double* G_A, stmf_stream_t stream);
 
 /*
+ * Sample-sharded evaluation. Every sum of Alg. 2 over samples (eq. Y, Lemma 3.5) splits over
+ * disjoint shards of V, so G devices holding shards V_g each compute their partial (w, Y), the
+ * partials are summed (one all-reduce of r + n r FP64 values), and lines 4-9 follow:
+ *
+ * stmf_fg_partial -- yw = [w; vec(Y)] summed over this shard: w_j = sum_l nu_l (v_l^T a_j)^d,
+ *   Y = sum_l nu_l (v_l^T A)^{d-1} v_l^T (n x r column-major after the r entries of w).
+ *   nu       device weights of this shard's samples, or NULL for nu_l = 1 / p_total.
+ *   p_total  the number of samples over all shards (used when nu is NULL; >= V->p).
+ *   yw       device, r + n r FP64 (out).
+ * stmf_fg_finish -- f, g_lambda, G_A from a summed yw (lines 4-9: B = A^T A, C, u, f, g).
+ *   n        features.   Other arguments as for stmf_fg.
+ * Both enqueue on `stream`; asynchronous.
+ */
+STMF_API stmf_status stmf_fg_partial(stmf_ctx_t ctx, const stmf_samples* V, const double* nu,
+                                     int64_t p_total, int32_t d, int64_t r, const double* lambda,
+                                     const double* A, double* yw, stmf_stream_t stream);
+STMF_API stmf_status stmf_fg_finish(stmf_ctx_t ctx, const double* yw, int64_t n, int32_t d,
+                                    int64_t r, const double* lambda, const double* A,
+                                    const double* alpha, double* f, double* g_lambda, double* G_A,
+                                    stmf_stream_t stream);
+
+/*
  * stmf_norm_x -- alpha = ||X||^2 = nu^T (V^T V)^d nu, Lemma 3.4 applied to X (Sec. 3.3), the
  * O(n p^2) constant of Alg. 2. Evaluated over the upper triangle of sample-tile pairs without
  * forming the p x p Gram matrix; per-tile sums are combined in FP64.

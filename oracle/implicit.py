@@ -49,9 +49,14 @@ def fg_implicit(nu, V, lam, A, d, alpha=0.0, p=None, chunk=DEFAULT_CHUNK, return
 
     Returns (f, g_lambda, G_A), and with return_parts=True also a dict of the intermediate
     quantities Y, w, B, C, u (for parity checks of the GPU path's pieces)."""
+    Y = ttsv_matrix(nu, V, _as_f64(A), d, p=p, chunk=chunk)  # line 2
+    return model_terms(Y, lam, A, d, alpha=alpha, return_parts=return_parts)
+
+
+def model_terms(Y, lam, A, d, alpha=0.0, return_parts=False):
+    """Alg. 2 lines 3-9 from Y (line 2): w, B, C, u, then f, g_lambda and G_A."""
     lam = _as_f64(lam)
     A = _as_f64(A)
-    Y = ttsv_matrix(nu, V, A, d, p=p, chunk=chunk)          # line 2
     w = np.einsum("ij,ij->j", A, Y)                         # line 3: w_j = a_j^T y_j
     B = A.T @ A                                             # line 4
     C = B ** (d - 1)                                        # line 5

@@ -144,6 +144,15 @@ cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s) {
+  const int nbB = (prm.r * prm.r + (RE * RY / 32) - 1) / (RE * RY / 32);
+  reduce_kernel<<<nbB, RE * RY, 0, s>>>(prm, prm.r + prm.n * prm.r, 0);  // B blocks only
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<<<(prm.n * prm.r + RT - 1) / RT, RT, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+
 cudaError_t reduce_scalar_launch(const double* partials, int count, double* out,
                                  int32_t* status, cudaStream_t s) {
   reduce_scalar_kernel<<<1, 32, 0, s>>>(partials, count, out, status);

@@ -93,7 +93,8 @@ size_t stmf::fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_
 stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double* nu, int d, int64_t r,
                              const double* lambda, const double* A, const double* alpha, double* f,
                              double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
-                             const int64_t* idx, int64_t n_idx) {
+                             const int64_t* idx, int64_t n_idx, double* yw_out,
+                             double nu_uniform) {
   stmf_status st = check_samples(c, V_in);
   if (st != STMF_OK) return st;
   if (idx && n_idx < 1) return fail(c, STMF_EINVAL, "the number of sampled rows must be >= 1");
@@ -103,7 +104,8 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   const stmf_samples* V = &Vs;
   if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
   if (r < 1 || r > 64) return fail(c, STMF_EINVAL, "r must be in [1, 64]");
-  if (!lambda || !A || !f || !g_lambda || !G_A) return fail(c, STMF_EINVAL, "NULL model or output pointer");
+  if (!lambda || !A || (!yw_out && (!f || !g_lambda || !G_A)))
+    return fail(c, STMF_EINVAL, "NULL model or output pointer");
   const int n = (int)V->n;
   FgPlan pl = plan_fg(c, V, r);
   if (idx && pl.tc) {  // gathers take the CUDA-core pass
@@ -122,7 +124,7 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   prm.V = V->data;
   prm.scale = V->scale;
   prm.nu = nu;
-  prm.nu_uniform = 1.0 / double(V->p);
+  prm.nu_uniform = nu_uniform > 0.0 ? nu_uniform : 1.0 / double(V->p);
   prm.A = A;
   prm.partials = partials;
   prm.p = V->p;
@@ -170,7 +172,12 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   mp.d = d;
   mp.status = c->status;
   mp.skip = skip;
-  e = stmf::model_terms_launch(mp, s);
+  if (yw_out) {  // partial sums only (one shard of a sample-sharded evaluation)
+    mp.yw = yw_out;
+    e = stmf::reduce_partials_launch(mp, s);
+  } else {
+    e = stmf::model_terms_launch(mp, s);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "model terms launch");
   return STMF_OK;
 }
@@ -324,6 +331,45 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   normalize_columns<<<(int)((r_hat + 7) / 8), 256, 0, s>>>(yw + r_hat, n, (int)r_hat, A0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "normalisation launch");
+  return STMF_OK;
+}
+
+stmf_status stmf_fg_partial(stmf_ctx_t c, const stmf_samples* V, const double* nu,
+                            int64_t p_total, int32_t d, int64_t r, const double* lambda,
+                            const double* A, double* yw, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  if (!yw) return fail(c, STMF_EINVAL, "yw is NULL");
+  if (!V || (!nu && p_total < V->p)) return fail(c, STMF_EINVAL, "p_total must be >= V->p");
+  return stmf::enqueue_fg(c, V, nu, d, r, lambda, A, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          reinterpret_cast<cudaStream_t>(stream), nullptr, 0, yw,
+                          nu ? 0.0 : 1.0 / double(p_total));
+}
+
+stmf_status stmf_fg_finish(stmf_ctx_t c, const double* yw, int64_t n, int32_t d, int64_t r,
+                           const double* lambda, const double* A, const double* alpha, double* f,
+                           double* g_lambda, double* G_A, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  if (!yw || !lambda || !A || !f || !g_lambda || !G_A)
+    return fail(c, STMF_EINVAL, "NULL argument");
+  if (n < 1 || n > 256 || r < 1 || r > 64 || d < 2 || d > 8)
+    return fail(c, STMF_EINVAL, "n, r or d out of range");
+  stmf_status st = ensure_ws(c, size_t(r) * size_t(r) * sizeof(double));
+  if (st != STMF_OK) return st;
+  stmf::ModelParams mp{};
+  mp.A = A;
+  mp.lambda = lambda;
+  mp.alpha = alpha;
+  mp.f = f;
+  mp.g_lambda = g_lambda;
+  mp.G_A = G_A;
+  mp.yw = const_cast<double*>(yw);
+  mp.bmat = static_cast<double*>(c->ws);
+  mp.n = (int)n;
+  mp.r = (int)r;
+  mp.d = d;
+  mp.status = c->status;
+  cudaError_t e = stmf::finish_launch(mp, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "finish launch");
   return STMF_OK;
 }
 

@@ -67,6 +67,8 @@ int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 // Sum the block partials only (no model terms): yw = sum_g partials[g].
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
+// Alg. 2 lines 4-9 from a given yw = [w; vec(Y)] (B = A^T A, then the outputs).
+cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
@@ -117,7 +119,8 @@ stmf_status ensure_workspace(stmf_ctx* c, size_t bytes);
 stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
                        const double* lambda, const double* A, const double* alpha, double* f,
                        double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
-                       const int64_t* idx = nullptr, int64_t n_idx = 0);
+                       const int64_t* idx = nullptr, int64_t n_idx = 0,
+                       double* yw_out = nullptr, double nu_uniform = 0.0);
 size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
 
 // Bytes of the device optimiser state for D unknowns and m pairs.

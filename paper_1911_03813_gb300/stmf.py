@@ -569,3 +569,42 @@ def rrf_start(V, r_hat, seed, stream=None, ctx=None):
     ctx.check(st, "stmf_rrf_start")
     del keep
     return A0
+
+
+def _declare_sharded(L):
+    vp = ctypes.c_void_p
+    L.stmf_fg_partial.argtypes = [vp, ctypes.POINTER(Samples), vp, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_int64, vp, vp, vp, vp]
+    L.stmf_fg_finish.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, vp, vp,
+                                 vp, vp, vp, vp, vp]
+    L.stmf_fg_partial.restype = ctypes.c_int
+    L.stmf_fg_finish.restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_sharded)
+
+
+def fg_partial(V, nu, p_total, d, lam, A, stream=None, ctx=None):
+    """stmf_fg_partial: this shard's [w; vec(Y)] as an (r + n r,) CUDA float64 tensor."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    r = lam.shape[0]
+    yw = torch.empty(r + desc.n * r, dtype=torch.float64, device=lam.device)
+    st = lib().stmf_fg_partial(ctx.handle, ctypes.byref(desc), _ptr(nu), int(p_total), int(d),
+                               int(r), _ptr(lam), _ptr(A), _ptr(yw), _stream(stream))
+    ctx.check(st, "stmf_fg_partial")
+    del keep
+    return yw
+
+
+def fg_finish(yw, n, d, lam, A, alpha=None, stream=None, ctx=None):
+    """stmf_fg_finish: f, g_lambda, G_A from a summed [w; vec(Y)]."""
+    ctx = ctx or default_context()
+    r = lam.shape[0]
+    f = torch.empty(1, dtype=torch.float64, device=lam.device)
+    gl = torch.empty(r, dtype=torch.float64, device=lam.device)
+    GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
+    st = lib().stmf_fg_finish(ctx.handle, _ptr(yw), int(n), int(d), int(r), _ptr(lam), _ptr(A),
+                              _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _stream(stream))
+    ctx.check(st, "stmf_fg_finish")
+    return f, gl, GA

@@ -227,3 +227,28 @@ def test_norm_x_tensor_core_parity(stmf, n, p, d, weights):
     torch.cuda.synchronize()
     assert stmf.default_context().device_status() == 0
     assert abs(got - ref) <= 2e-6 * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("bf16", 1e-5)])
+def test_sharded_partials_on_one_gpu(stmf, dtype, tol):
+    """Two shards evaluated one after the other on this GPU, their partials summed and finished,
+    equal the single evaluation on all samples (the sample-sharded design, emulated)."""
+    from paper_1911_03813_gb300 import sharded
+    n, p, r, d = 40, 30001, 5, 4
+    data = inputs.gmm(n, p, 5, 0.1, seed=77)
+    lam, A = inputs.random_model(n, r, seed=78)
+    lam_t = torch.tensor(lam, device="cuda")
+    A_t = torch.tensor(np.ascontiguousarray(A.T), device="cuda").T
+    full = inputs.to_storage(data["V"], dtype, device="cuda")
+    f0, gl0, GA0 = stmf.fg(full, None, d, lam_t, A_t)
+    yw = None
+    for k in range(2):
+        lo, hi = sharded.shard_bounds(p, 2, k)
+        part = inputs.to_storage(data["V"][lo:hi], dtype, device="cuda")
+        y = stmf.fg_partial(part, None, p, d, lam_t, A_t)
+        yw = y if yw is None else yw + y
+    f1, gl1, GA1 = stmf.fg_finish(yw, n, d, lam_t, A_t)
+    torch.cuda.synchronize()
+    assert abs(f1.item() - f0.item()) <= tol * max(1.0, abs(f0.item()))
+    assert float(torch.linalg.norm(GA1 - GA0) / torch.linalg.norm(GA0)) <= tol
+    assert float(torch.linalg.norm(gl1 - gl0) / torch.linalg.norm(gl0)) <= tol
