@@ -140,6 +140,23 @@ STMF_API stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double
                     double* f, double* g_lambda, double* G_A, stmf_stream_t stream);
 
 /*
+ * stmf_fg_host -- stmf_fg with every array in HOST memory (the end-to-end call). V (and nu, the
+ * E4M3 scales) are streamed to the device in chunks of about 256 MB through three library-owned
+ * staging buffers on two copy streams, so the copy of one chunk overlaps the pass over the
+ * previous ones; chunk partials are summed in FP64 in chunk order; f, g_lambda and G_A are
+ * copied back. Use pinned host memory for V: from pageable memory the copies do not overlap.
+ *  V        host samples (stmf_samples with host pointers).   nu  host p FP64 or NULL (1/p).
+ *  lambda   host r.   A  host n x r column-major.   alpha  the constant of line 7 (0: shifted).
+ *  f, g_lambda, G_A   host outputs.
+ * Synchronous: returns when the outputs are in host memory. The first call, and a call with
+ * larger rows than before, allocates the staging buffers (synchronising the device).
+ */
+STMF_API stmf_status stmf_fg_host(stmf_ctx_t ctx, const stmf_samples* V, const double* nu,
+                                  int32_t d, int64_t r, const double* lambda, const double* A,
+                                  double alpha, double* f, double* g_lambda, double* G_A,
+                                  stmf_stream_t stream);
+
+/*
  * Sample-sharded evaluation. Every sum of Alg. 2 over samples (eq. Y, Lemma 3.5) splits over
  * disjoint shards of V, so G devices holding shards V_g each compute their partial (w, Y), the
  * partials are summed (one all-reduce of r + n r FP64 values), and lines 4-9 follow:

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(RE * RY) reduce_kernel(const ModelParams prm, 
       double t = red[0][x];
 #pragma unroll
       for (int k = 1; k < RY; ++k) t += red[k][x];
-      prm.yw[e] = t;
+      prm.yw[e] = prm.accumulate ? prm.yw[e] + t : t;
     }
     return;
   }

@@ -94,7 +94,7 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
                              const double* lambda, const double* A, const double* alpha, double* f,
                              double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
                              const int64_t* idx, int64_t n_idx, double* yw_out,
-                             double nu_uniform) {
+                             double nu_uniform, bool accumulate) {
   stmf_status st = check_samples(c, V_in);
   if (st != STMF_OK) return st;
   if (idx && n_idx < 1) return fail(c, STMF_EINVAL, "the number of sampled rows must be >= 1");
@@ -174,6 +174,7 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   mp.skip = skip;
   if (yw_out) {  // partial sums only (one shard of a sample-sharded evaluation)
     mp.yw = yw_out;
+    mp.accumulate = accumulate ? 1 : 0;
     e = stmf::reduce_partials_launch(mp, s);
   } else {
     e = stmf::model_terms_launch(mp, s);
@@ -237,6 +238,14 @@ stmf_status stmf_destroy(stmf_ctx_t c) {
   if (c->fit_ws) cudaFree(c->fit_ws);
   if (c->status) cudaFree(c->status);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+  for (int k = 0; k < 3; ++k) {
+    if (c->stage[k]) cudaFree(c->stage[k]);
+    if (c->copied[k]) cudaEventDestroy(c->copied[k]);
+    if (c->consumed[k]) cudaEventDestroy(c->consumed[k]);
+  }
+  for (int k = 0; k < 2; ++k)
+    if (c->copy_stream[k]) cudaStreamDestroy(c->copy_stream[k]);
+  if (c->host_small) cudaFree(c->host_small);
   delete c;
   return STMF_OK;
 }
@@ -370,6 +379,124 @@ stmf_status stmf_fg_finish(stmf_ctx_t c, const double* yw, int64_t n, int32_t d,
   mp.status = c->status;
   cudaError_t e = stmf::finish_launch(mp, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "finish launch");
+  return STMF_OK;
+}
+
+stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32_t d,
+                         int64_t r, const double* lambda, const double* A, double alpha,
+                         double* f, double* g_lambda, double* G_A, stmf_stream_t stream) {
+  if (!c) return STMF_EINVAL;
+  if (!V || !V->data || !lambda || !A || !f || !g_lambda || !G_A)
+    return fail(c, STMF_EINVAL, "NULL argument");
+  const int eb = stmf::elem_bytes(V->dtype);
+  if (eb == 0 || V->n < 1 || V->n > 256 || V->p < 1 || V->ld < V->n || (V->ld * eb) % 16 != 0)
+    return fail(c, STMF_EINVAL, "invalid samples");
+  if ((V->dtype == STMF_E4M3) != (V->scale != nullptr))
+    return fail(c, STMF_EINVAL, "E4M3 samples need scales (and only they)");
+  if (d < 2 || d > 8 || r < 1 || r > 64) return fail(c, STMF_EINVAL, "d or r out of range");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = V->n, p = V->p;
+  const size_t row_bytes = size_t(V->ld) * eb;
+  // chunks of about 256 MB (a whole number of 128-sample tiles), three staging buffers
+  int64_t rows = (int64_t(256) << 20) / int64_t(row_bytes);
+  rows = rows < 128 ? 128 : rows / 128 * 128;
+  if (rows > p) rows = p;
+  const size_t chunk_bytes = size_t(rows) * row_bytes;
+  const size_t extra = size_t(rows) * (sizeof(double) + sizeof(float));  // nu and scale slices
+  const size_t need_stage = chunk_bytes + extra + 256;
+  if (need_stage > c->stage_bytes) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, STMF_ECUDA, "sync");
+    for (int k = 0; k < 3; ++k) {
+      if (c->stage[k]) cudaFree(c->stage[k]);
+      c->stage[k] = nullptr;
+    }
+    c->stage_bytes = 0;
+    for (int k = 0; k < 3; ++k)
+      if (cudaMalloc(&c->stage[k], need_stage) != cudaSuccess)
+        return fail(c, STMF_ENOMEM, "cudaMalloc of the staging buffers failed");
+    c->stage_bytes = need_stage;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (!c->copied[k] && cudaEventCreateWithFlags(&c->copied[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, STMF_ECUDA, "event");
+    if (!c->consumed[k] &&
+        cudaEventCreateWithFlags(&c->consumed[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, STMF_ECUDA, "event");
+  }
+  for (int k = 0; k < 2; ++k)
+    if (!c->copy_stream[k] &&
+        cudaStreamCreateWithFlags(&c->copy_stream[k], cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, STMF_ECUDA, "stream");
+  // small device buffers: lambda, A, alpha, yw, f, g_lambda, G_A
+  const size_t L = size_t(r) + size_t(n) * r;
+  const size_t small = sizeof(double) * (r + n * r + 1 + L + 1 + r + n * r);
+  if (small > c->host_small_bytes) {
+    if (c->host_small) cudaFree(c->host_small);
+    c->host_small = nullptr;
+    c->host_small_bytes = 0;
+    if (cudaMalloc(&c->host_small, small) != cudaSuccess)
+      return fail(c, STMF_ENOMEM, "cudaMalloc failed");
+    c->host_small_bytes = small;
+  }
+  double* d_lam = static_cast<double*>(c->host_small);
+  double* d_A = d_lam + r;
+  double* d_alpha = d_A + n * r;
+  double* d_yw = d_alpha + 1;
+  double* d_f = d_yw + L;
+  double* d_gl = d_f + 1;
+  double* d_GA = d_gl + r;
+  cudaMemcpyAsync(d_lam, lambda, sizeof(double) * r, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_A, A, sizeof(double) * n * r, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaEvent_t start_ev = c->copied[2];
+  cudaEventRecord(start_ev, s);  // the copy streams start after the previous work on `s`
+  for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(c->copy_stream[k], start_ev, 0);
+  const int64_t nchunks = (p + rows - 1) / rows;
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    const int k = int(ch % 3);
+    cudaStream_t cs = c->copy_stream[ch % 2];
+    const int64_t lo = ch * rows, cnt = (lo + rows <= p) ? rows : p - lo;
+    unsigned char* buf = static_cast<unsigned char*>(c->stage[k]);
+    if (ch >= 3) cudaStreamWaitEvent(cs, c->consumed[k], 0);  // the pass over chunk ch-3 is done
+    cudaMemcpyAsync(buf, static_cast<const unsigned char*>(V->data) + size_t(lo) * row_bytes,
+                    size_t(cnt) * row_bytes, cudaMemcpyHostToDevice, cs);
+    double* nu_d = reinterpret_cast<double*>(buf + chunk_bytes);
+    float* sc_d = reinterpret_cast<float*>(buf + chunk_bytes + size_t(rows) * sizeof(double));
+    if (nu) cudaMemcpyAsync(nu_d, nu + lo, sizeof(double) * cnt, cudaMemcpyHostToDevice, cs);
+    if (V->scale)
+      cudaMemcpyAsync(sc_d, V->scale + lo, sizeof(float) * cnt, cudaMemcpyHostToDevice, cs);
+    cudaEventRecord(c->copied[k], cs);
+    cudaStreamWaitEvent(s, c->copied[k], 0);
+    stmf_samples chunk = *V;
+    chunk.data = buf;
+    chunk.p = cnt;
+    chunk.scale = V->scale ? sc_d : nullptr;
+    stmf_status st = stmf::enqueue_fg(c, &chunk, nu ? nu_d : nullptr, d, r, d_lam, d_A, nullptr,
+                                      nullptr, nullptr, nullptr, nullptr, s, nullptr, 0, d_yw,
+                                      nu ? 0.0 : 1.0 / double(p), ch > 0);
+    if (st != STMF_OK) return st;
+    cudaEventRecord(c->consumed[k], s);
+  }
+  stmf::ModelParams mp{};
+  mp.A = d_A;
+  mp.lambda = d_lam;
+  mp.alpha = d_alpha;
+  mp.f = d_f;
+  mp.g_lambda = d_gl;
+  mp.G_A = d_GA;
+  mp.yw = d_yw;
+  mp.bmat = static_cast<double*>(c->ws);  // the passes are done with the workspace by now
+  mp.n = (int)n;
+  mp.r = (int)r;
+  mp.d = d;
+  mp.status = c->status;
+  cudaError_t e = stmf::finish_launch(mp, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "finish launch");
+  cudaMemcpyAsync(f, d_f, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(g_lambda, d_gl, sizeof(double) * r, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(G_A, d_GA, sizeof(double) * n * r, cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stmf_fg_host");
   return STMF_OK;
 }
 

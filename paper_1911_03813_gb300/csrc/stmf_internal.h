@@ -44,6 +44,7 @@ struct ModelParams {
   int n, r, d;
   int32_t* status;
   const int32_t* skip;     // as in FgParams
+  int accumulate;          // reduce_partials: yw += sum (instead of yw = sum)
 };
 
 struct GramParams {
@@ -108,6 +109,14 @@ struct stmf_ctx {
   bool profiling = false;    // record events around each fused pass
   std::vector<cudaEvent_t> ev_pool;  // recorded pairs: [2k] start, [2k+1] end
   size_t ev_used = 0;
+  // host-streaming evaluation (stmf_fg_host): staging buffers, copy streams, events
+  void* stage[3] = {nullptr, nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};
+  cudaEvent_t copied[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t consumed[3] = {nullptr, nullptr, nullptr};
+  void* host_small = nullptr;  // device: lambda, A, alpha, yw, outputs
+  size_t host_small_bytes = 0;
 };
 
 namespace stmf {
@@ -120,7 +129,8 @@ stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int
                        const double* lambda, const double* A, const double* alpha, double* f,
                        double* g_lambda, double* G_A, const int32_t* skip, cudaStream_t s,
                        const int64_t* idx = nullptr, int64_t n_idx = 0,
-                       double* yw_out = nullptr, double nu_uniform = 0.0);
+                       double* yw_out = nullptr, double nu_uniform = 0.0,
+                       bool accumulate = false);
 size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
 
 // Bytes of the device optimiser state for D unknowns and m pairs.

@@ -608,3 +608,44 @@ def fg_finish(yw, n, d, lam, A, alpha=None, stream=None, ctx=None):
                               _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _stream(stream))
     ctx.check(st, "stmf_fg_finish")
     return f, gl, GA
+
+
+def _declare_host(L):
+    vp = ctypes.c_void_p
+    L.stmf_fg_host.argtypes = [vp, ctypes.POINTER(Samples), vp, ctypes.c_int32, ctypes.c_int64,
+                               vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    L.stmf_fg_host.restype = ctypes.c_int
+
+
+_extra_declarers.append(_declare_host)
+
+
+def fg_host(V, nu, d, lam, A, alpha=0.0, stream=None, ctx=None):
+    """stmf_fg_host: the evaluation with host inputs and outputs. V: torch CPU tensor p x ld of a
+    storage dtype (pin it for overlapped copies), or a storage dict with CPU tensors; lam (r,) and
+    A (n, r) float64 CPU/NumPy. Returns host NumPy (f, g_lambda, G_A)."""
+    import numpy as np
+    ctx = ctx or default_context()
+    scale = None
+    n = None
+    if isinstance(V, dict):
+        n, scale, V = V["n"], V.get("scale"), V["data"]
+    if V.is_cuda:
+        raise ValueError("fg_host takes samples in host memory")
+    dt = _TORCH_DTYPE[V.dtype]
+    n = V.shape[1] if n is None else n
+    desc = Samples(V.data_ptr(), scale.data_ptr() if scale is not None else None, int(n),
+                   int(V.shape[0]), int(V.stride(0)), dt, 0)
+    lam_h = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+    A_h = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    nu_h = None if nu is None else np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    r = lam_h.shape[0]
+    f = np.empty(1)
+    gl = np.empty(r)
+    GA = np.empty((n, r), order="F")
+    st = lib().stmf_fg_host(ctx.handle, ctypes.byref(desc),
+                            None if nu_h is None else nu_h.ctypes.data, int(d), int(r),
+                            lam_h.ctypes.data, A_h.ctypes.data, float(alpha), f.ctypes.data,
+                            gl.ctypes.data, GA.ctypes.data, _stream(stream))
+    ctx.check(st, "stmf_fg_host")
+    return float(f[0]), gl, GA

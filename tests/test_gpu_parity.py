@@ -252,3 +252,25 @@ def test_sharded_partials_on_one_gpu(stmf, dtype, tol):
     assert abs(f1.item() - f0.item()) <= tol * max(1.0, abs(f0.item()))
     assert float(torch.linalg.norm(GA1 - GA0) / torch.linalg.norm(GA0)) <= tol
     assert float(torch.linalg.norm(gl1 - gl0) / torch.linalg.norm(gl0)) <= tol
+
+
+@pytest.mark.parametrize("dtype,n,p,r,d,tol", [("bf16", 256, 600000, 16, 4, 4e-5),
+                                               ("f64", 30, 70001, 3, 3, 1e-12),
+                                               ("e4m3", 64, 300000, 8, 3, 4e-5)])
+def test_fg_host_streaming(stmf, dtype, n, p, r, d, tol):
+    """Host inputs streamed in chunks (several chunks at these sizes for 1-byte and 2-byte
+    samples) give the oracle's result."""
+    data = inputs.gmm(n, p, 8, 0.1, seed=p + 1)
+    st = inputs.to_storage(data["V"], dtype, device="cpu")
+    st["data"] = st["data"].pin_memory()
+    if st["scale"] is not None:
+        st["scale"] = st["scale"].pin_memory()
+    lam, A = inputs.random_model(n, r, seed=r)
+    nu = inputs.positive_weights(p, seed=3) if dtype == "f64" else None
+    f, gl, GA = stmf.fg_host(st, nu, d, lam, A, alpha=0.5)
+    Vd = decoded(st)
+    f_ref, gl_ref, GA_ref, parts = oracle.fg_implicit(nu, Vd.T, lam, A, d, alpha=0.5,
+                                                      return_parts=True)
+    S = 0.5 + abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
+    assert abs(f - f_ref) <= tol * S
+    assert rel(gl, gl_ref) <= tol and rel(GA, GA_ref) <= tol
