@@ -406,7 +406,23 @@ def main():
             stmf.fg_host(st_h, None, D, lam_h, A_h)
         el = time.perf_counter() - t0
         barrier()
+        # the host-to-device link's own copy rate (one pinned 1 GiB copy, CUDA events): the
+        # end-to-end call moves V over this link every step, so it bounds the e2e rate
+        lk_h = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+        lk_d = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        lk_d.copy_(lk_h, non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            lk_d.copy_(lk_h, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        link_gbs = 3 * (1 << 30) / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del lk_h, lk_d
+        h2d_gbs = (bytes16 + 8 * (R + R * N_FEAT + 1)) * args.e2e_steps / el / 1e9
         e2e = {"value": world * args.e2e_steps / el, "unit": "evals/s",
+               "h2d_gbs": round(h2d_gbs, 1), "link_h2d_gbs_measured": round(link_gbs, 1),
+               "link_frac": round(h2d_gbs / link_gbs, 3),
                "h2d_bytes_per_step": bytes16 + 8 * (R + R * N_FEAT + 1),
                "d2h_bytes_per_step": 8 * (1 + R + R * N_FEAT),
                "call": "stmf_fg_host (pinned host V, chunked H2D overlapped with the passes)"}

@@ -7,9 +7,10 @@
 //
 // Per 128-sample tile (V_t: 128 samples x n features, BF16, staged by TMA with the 128-byte
 // swizzle, one 16 KB region per 64 features):
-//   MMA1  Z  = V_t [A_hi | A_lo]           M = 128 samples, N = 2 RP, K = n     (TMEM)
+//   MMA1  Z  = V_t [A_hi, A_lo]            M = 128 samples, N = 2 RP, K = n     (TMEM)
 //   epi   z = Z_hi + Z_lo;  W = nu z^{d-1} (split into BF16 hi | lo);  w += nu z^d
-//   MMA2  Y += V_t^T [W_hi | W_lo]         M = 128 features (per block), N = 2 RP, K = 128
+//   end   w += d sum_i Y_ij (A - A_hi - A_lo)_ij   (first-order correction for the split of A)
+//   MMA2  Y += V_t^T [W_hi, W_lo]          M = 128 features (per block), N = 2 RP, K = 128
 // The same shared-memory tile is the K-major A operand of MMA1 and the MN-major A operand of
 // MMA2. A (FP64) is split once per CTA into BF16 hi/lo halves so that A_hi + A_lo carries ~16
 // significant bits; W is split the same way per tile. Both halves ride in one MMA along N, so
@@ -44,6 +45,12 @@ constexpr int NTHREADS = 96 + NEPI;    // producer warp, MMA1 warp, MMA2 warp, e
 constexpr int NCONV = 4;               // FP8 samples: warps that widen E4M3 tiles to BF16
 constexpr int NTHREADS_FP8 = NTHREADS + 32 * NCONV;
 constexpr int Q_BYTES = TM * 128;      // one 128-feature region of an E4M3 tile (16 KB)
+// Z accumulators per tile: MMA1's K steps are split ZC ways and the partial products summed in
+// the epilogue with round-to-nearest. The tensor cores' FP32 accumulation truncates, so a long
+// run of accumulations biases |z| low (measured at n = 256: 1.6e-6 relative with one
+// accumulator, 0.8e-6 with two, 0.4e-6 with four); w = sum nu z^d inherits d times that bias.
+// Two accumulators halve it for about 1% of the pass time.
+constexpr int ZC = 2;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
 struct TcExtra {
@@ -55,11 +62,16 @@ struct TcExtra {
   int smem_bytes;
   int nq;         // E4M3 samples: 128-feature regions per tile (ceil(n / 128))
   int qstages;    // E4M3 samples: TMA ring depth of E4M3 tiles
+  int kpz;        // K steps (16 features each) per Z accumulator (ZC accumulators per tile)
 };
 
+// Column order along N (rows of the A and W splits, columns of Z and Y in TMEM): components are
+// grouped by epilogue warpgroup, hi and lo side by side, so one TMEM load brings a warpgroup's
+// hi and lo values: column of (component j, part) = (j / CPG) 2 CPG + part CPG + j % CPG.
 template <int RP>
 struct Cfg {
-  static constexpr int N = 2 * RP;            // MMA N: [hi | lo]
+  static constexpr int CPG = RP / EG;         // components per epilogue warpgroup
+  static constexpr int N = 2 * RP;            // MMA N: hi and lo of every component
   static constexpr int W_REG = N * 128;       // one 64-sample region of W (N rows)
   static constexpr int A_REG = N * 128;       // one 64-feature region of the A split
 };
@@ -81,10 +93,12 @@ __device__ __forceinline__ float ipow_f(float z, int e) {
 
 template <int C>
 __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
-  if constexpr (C == 4) {
+  if constexpr (C == 8) {
+    tc::tmem_ld8(taddr, v);
+  } else if constexpr (C == 4) {
     tc::tmem_ld4(taddr, v);
   } else {
-    static_assert(C == 2, "2 or 4 columns per load");
+    static_assert(C == 2, "2, 4 or 8 columns per load");
     tc::tmem_ld2(taddr, v);
   }
 }
@@ -106,6 +120,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   unsigned char* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
 
   const int S = ex.stages, nreg = ex.nreg, nload = ex.nload;
+  const int kpz = ex.kpz;
   const int n = prm.n, r = prm.r, d = prm.d;
   const uint32_t stage_bytes = uint32_t(nreg) * REG_BYTES;
   unsigned char* sV = base;
@@ -156,15 +171,17 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
   if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
 
-  // A split: rows [0, RP) hold BF16(a_j), rows [RP, 2 RP) hold BF16(a_j - BF16(a_j)); K = feature.
+  // A split: the hi row of component j holds BF16(a_j), its lo row BF16(a_j - BF16(a_j)); K =
+  // feature.
   {
     const int kext = nreg * 64;
     for (int e = tid; e < N * kext; e += NT) {
       const int row = e / kext, k = e - row * kext;
-      const int j = row % RP;
+      const int grp = row / (2 * C::CPG), part = (row / C::CPG) & 1;
+      const int j = grp * C::CPG + row % C::CPG;
       double a = (j < r && k < n) ? prm.A[k + size_t(n) * j] : 0.0;
       const __nv_bfloat16 hi = __double2bfloat16(a);
-      const __nv_bfloat16 v = row < RP ? hi : __double2bfloat16(a - (double)__bfloat162float(hi));
+      const __nv_bfloat16 v = part == 0 ? hi : __double2bfloat16(a - (double)__bfloat162float(hi));
       *reinterpret_cast<__nv_bfloat16*>(sA + (k >> 6) * C::A_REG + tc::sw128_offset(row, k & 63)) = v;
     }
     // regions of each V stage that TMA never loads (features beyond the last 64-block) are zero
@@ -242,11 +259,20 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         if (!ok) break;
         tc::tc_fence_after();
         const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
-        for (int kk = 0; kk < k1; ++kk) {
-          const uint64_t ad = tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
-          const uint64_t bd =
-              tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
-          tc::mma_bf16(tmem + zb * N, ad, bd, idesc1, kk > 0 ? 1u : 0u);
+        // accumulator c takes K steps [c kpz, min((c + 1) kpz, k1)); one that gets none (small
+        // n) takes step c kpz alone, which lies in the zero padding of both operands, so every
+        // accumulator is written
+        for (int c = 0; c < ZC; ++c) {
+          const uint32_t dZ = tmem + uint32_t(zb * ZC + c) * N;
+          const int kb = c * kpz;
+          const int ke = kb + kpz < k1 ? kb + kpz : (kb < k1 ? k1 : kb + 1);
+          for (int kk = kb; kk < ke; ++kk) {
+            const uint64_t ad =
+                tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
+            const uint64_t bd =
+                tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
+            tc::mma_bf16(dZ, ad, bd, idesc1, kk > kb ? 1u : 0u);
+          }
         }
         tc::mma_commit(&zfull[zb]);
       }
@@ -273,7 +299,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
         const uint32_t wbb = sw0 + uint32_t(wb) * 2 * C::W_REG;
         for (int mb = 0; mb < nmb; ++mb) {
-          const uint32_t dY = tmem + 2 * N + uint32_t(yb * 2 + mb) * N;
+          const uint32_t dY = tmem + uint32_t(2 * ZC + yb * 2 + mb) * N;
           for (int kk = 0; kk < TM / 16; ++kk) {
             const uint64_t ad = tc::sdesc_sw128(vb + uint32_t(2 * mb) * REG_BYTES + kk * 2048,
                                                 REG_BYTES, 1024);
@@ -346,7 +372,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     // ------------------------------------------------------------------ epilogue
     // EG warpgroups; warpgroup g owns components [g*CPG, (g+1)*CPG) of every sample of the tile
     // (thread = TMEM lane = sample), so the per-tile work of one thread is CPG components.
-    constexpr int CPG = RP / EG;
+    constexpr int CPG = C::CPG;
     const int g = (warp - 3) >> 2;
     const int q = warp & 3;            // TMEM lane quarter this warp may access
     const int L = 32 * q + lane;       // sample within the tile / feature within the M-block
@@ -375,15 +401,14 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
 #pragma unroll
       for (int mb = 0; mb < 2; ++mb) {
         if (mb < nmb) {
-          float yh[CPG], yl[CPG];
-          const uint32_t ycol = tmem + 2 * N + uint32_t(yb * 2 + mb) * N + j0 + lane_off;
-          tmem_load_cols<CPG>(ycol, yh);
-          tmem_load_cols<CPG>(ycol + RP, yl);
+          float yv[2 * CPG];  // hi of the group's components, then lo
+          tmem_load_cols<2 * CPG>(tmem + uint32_t(2 * ZC + yb * 2 + mb) * N + 2 * j0 + lane_off,
+                                  yv);
           tc::tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < CPG; ++c) {
-            kahan_add(ys[mb][c], yc[mb][c], yh[c]);
-            kahan_add(ys[mb][c], yc[mb][c], yl[c]);
+            kahan_add(ys[mb][c], yc[mb][c], yv[c]);
+            kahan_add(ys[mb][c], yc[mb][c], yv[CPG + c]);
           }
         }
       }
@@ -419,9 +444,12 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         break;
       }
       tc::tc_fence_after();
-      float zh[CPG], zl[CPG];
-      tmem_load_cols<CPG>(tmem + zb * N + j0 + lane_off, zh);
-      tmem_load_cols<CPG>(tmem + zb * N + RP + j0 + lane_off, zl);
+      // z = sum over the Z accumulators of (hi + lo), rounded to nearest in FP32: each
+      // accumulator takes only kpz truncating tensor-core accumulations
+      float zv[ZC][2 * CPG];  // per accumulator: hi of the group's components, then lo
+#pragma unroll
+      for (int c = 0; c < ZC; ++c)
+        tmem_load_cols<2 * CPG>(tmem + uint32_t(zb * ZC + c) * N + 2 * j0 + lane_off, zv[c]);
       tc::tmem_ld_wait();
       tc::tc_fence_before();
       __syncwarp();
@@ -429,7 +457,9 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       float wv[CPG];
 #pragma unroll
       for (int c = 0; c < CPG; ++c) {
-        const float zz = zh[c] + zl[c];
+        float zz = zv[0][c] + zv[0][CPG + c];
+#pragma unroll
+        for (int k = 1; k < ZC; ++k) zz += zv[k][c] + zv[k][CPG + c];
         const float t = ipow_f(zz, d - 1);
         wv[c] = nu_s * t;
         wacc[c] += wv[c] * zz;
@@ -440,12 +470,11 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       }
       unsigned char* wbuf = sW + size_t(wb) * 2 * C::W_REG + wcol;
 #pragma unroll
-      for (int c = 0; c < CPG; ++c) {
-        const int j = j0 + c;
+      for (int c = 0; c < CPG; ++c) {  // rows 2 j0 + c (hi) and 2 j0 + CPG + c (lo)
         const __nv_bfloat16 hi = __float2bfloat16_rn(wv[c]);
         const __nv_bfloat16 lo = __float2bfloat16_rn(wv[c] - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(j, L & 63)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(RP + j, L & 63)) = lo;
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(2 * j0 + c, L & 63)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(2 * j0 + CPG + c, L & 63)) = lo;
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
@@ -473,19 +502,32 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       fail();
     } else {
       double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+      // First-order correction of w for the split of A: MMA1 contracts with
+      // A^ = A_hi + A_lo = A - dA (|dA| <= 2^-17 |A|), so z^ = z - v^T da_j and
+      // sum nu z^d = sum nu z^^d + d sum_i Y_ij dA_ij + O(|dA|^2), with Y the block's own partial
+      // of eq. Y. The correction is linear in Y, so block partials stay additive.
+      double corr[CPG];
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) corr[c] = 0.0;
 #pragma unroll
       for (int mb = 0; mb < 2; ++mb) {
         const int i = 128 * mb + L;
         if (mb < nmb && i < n) {
 #pragma unroll
           for (int c = 0; c < CPG; ++c)
-            if (j0 + c < r)
-              part[r + i + size_t(n) * (j0 + c)] = (double)ys[mb][c] - (double)yc[mb][c];
+            if (j0 + c < r) {
+              const double y = (double)ys[mb][c] - (double)yc[mb][c];
+              part[r + i + size_t(n) * (j0 + c)] = y;
+              const double a = prm.A[i + size_t(n) * (j0 + c)];
+              const double hi = (double)__bfloat162float(__double2bfloat16(a));
+              const double lo = (double)__bfloat162float(__double2bfloat16(a - hi));
+              corr[c] += y * ((a - hi) - lo);
+            }
         }
       }
 #pragma unroll
       for (int c = 0; c < CPG; ++c) {
-        double x = (double)ws[c] - (double)wc[c];
+        double x = (double)ws[c] - (double)wc[c] + double(d) * corr[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) wred[q * RP + j0 + c] = x;
@@ -533,8 +575,13 @@ TcExtra plan(int n, int r, bool fp8) {
   int S = (232448 - fixed) / stage;
   if (S > 8) S = 8;
   ex.stages = S;
-  ex.flush = 16;
-  int cols = 6 * N;
+  ex.flush = 8;  // fewer truncating accumulations of Y in TMEM between FP32 folds
+  // MMA1 runs K = n in k1 steps of 16 features, split over ZC accumulators. An accumulator with
+  // no step of its own takes step c kpz <= 9, inside the zero padding: the V stage holds
+  // nreg * 64 >= 128 features (zero past n) and the A split is zero past n as well.
+  const int k1 = (n + 15) / 16;
+  ex.kpz = (k1 + ZC - 1) / ZC;
+  int cols = (2 * ZC + 4) * N;
   int pow2 = 32;
   while (pow2 < cols) pow2 <<= 1;
   ex.tmem_cols = pow2;
