@@ -77,9 +77,11 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
 
   const int n = (int)V->n;
   const bool tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
-  if (!tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > 232448) return STMF_EINVAL;
-  int grid = tc ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, sms)
-                : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, sms);
+  const bool f32 = !tc && stmf::fg_f32_supported(V->dtype, n, (int)r);
+  if (!tc && !f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > 232448) return STMF_EINVAL;
+  int grid = tc    ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, sms)
+             : f32 ? stmf::fg_f32_grid(n, V->p, sms)
+                   : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, sms);
   // the partials of `grid` blocks plus the reduced (w, Y) must fit the fixed scratch; the pass is
   // persistent, so fewer blocks only means fewer tiles in flight
   const size_t L = size_t(r) + size_t(n) * size_t(r);
@@ -112,8 +114,9 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   prm.r_pad = (int)((r + 3) / 4 * 4);
   prm.flush_tiles = 16;
   prm.status = status_word;
-  cudaError_t e = tc ? stmf::fg_tc_launch(V->dtype, prm, grid, s)
-                     : stmf::fg_simt_launch(V->dtype, prm, grid, s);
+  cudaError_t e = tc    ? stmf::fg_tc_launch(V->dtype, prm, grid, s)
+                  : f32 ? stmf::fg_f32_launch(prm, grid, s)
+                        : stmf::fg_simt_launch(V->dtype, prm, grid, s);
   if (e != cudaSuccess) return STMF_ECUDA;
 
   stmf::ModelParams mp{};

@@ -54,7 +54,8 @@ stmf_status ensure_ws(stmf_ctx* c, size_t bytes) {
 }
 
 struct FgPlan {
-  bool tc = false;
+  bool tc = false;   // tensor-core pass (BF16, E4M3)
+  bool f32 = false;  // register-blocked FP32 pass
   int grid = 0;
   size_t partial_doubles = 0;  // grid * L
   size_t L = 0;
@@ -64,8 +65,10 @@ FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
   FgPlan pl;
   const int n = (int)V->n;
   pl.tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
-  pl.grid = pl.tc ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, c->num_sms)
-                  : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
+  pl.f32 = !pl.tc && stmf::fg_f32_supported(V->dtype, n, (int)r);
+  pl.grid = pl.tc    ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, c->num_sms)
+            : pl.f32 ? stmf::fg_f32_grid(n, V->p, c->num_sms)
+                     : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
   pl.L = size_t(r) + size_t(n) * size_t(r);
   pl.partial_doubles = size_t(pl.grid) * pl.L;
   return pl;
@@ -113,7 +116,7 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
     pl.grid = stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
     pl.partial_doubles = size_t(pl.grid) * pl.L;
   }
-  if (!pl.tc && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
+  if (!pl.tc && !pl.f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
     return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
   st = ensure_ws(c, fg_ws_bytes(pl, r));
   if (st != STMF_OK) return st;
@@ -151,8 +154,9 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
       c->ev_used += 2;
     }
   }
-  cudaError_t e = pl.tc ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
-                        : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
+  cudaError_t e = pl.tc    ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
+                  : pl.f32 ? stmf::fg_f32_launch(prm, pl.grid, s)
+                           : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
   if (ev_end) cudaEventRecord(ev_end, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused pass launch");
 

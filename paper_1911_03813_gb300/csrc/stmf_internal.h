@@ -70,6 +70,10 @@ cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s)
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
 // Alg. 2 lines 4-9 from a given yw = [w; vec(Y)] (B = A^T A, then the outputs).
 cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s);
+// Register-blocked CUDA-core pass for FP32 samples (n <= 256, r <= 16; gathers supported).
+bool fg_f32_supported(int dtype, int n, int r);
+int fg_f32_grid(int n, int64_t p, int num_sms);
+cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
