@@ -77,7 +77,7 @@ typedef enum {
 typedef struct {
   const void* data;   /* device; p rows of ld elements of `dtype`; 16-byte aligned */
   const float* scale; /* device; p FP32 per-sample scales for STMF_E4M3, else NULL */
-  int64_t n;          /* features per sample, 1 <= n <= 256 */
+  int64_t n;          /* features per sample, 1 <= n <= 512 (see stmf_fg for n x r limits) */
   int64_t p;          /* number of samples, p >= 1 */
   int64_t ld;         /* row stride in elements, ld >= n, ld * sizeof(dtype) % 16 == 0 */
   int32_t dtype;      /* stmf_dtype */
@@ -123,8 +123,13 @@ STMF_API stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, in
  * Powers of matrices are element-wise (Sec. 2).
  *
  *  V        samples (see stmf_samples). BF16 and E4M3 samples are contracted on the tensor
- *           cores with FP32 accumulation; F32 with FP32 FMA; F64 with FP64 FMA. Per-block
- *           partial sums are combined in FP64 and lines 3-9 run in FP64.
+ *           cores with FP32 accumulation (n <= 256, r <= 16); F32 with FP32 FMA; F64 with FP64
+ *           FMA; other shapes on the CUDA cores in FP32 (FP64 for F64). Per-block partial sums
+ *           are combined in FP64 and lines 3-9 run in FP64. The CUDA-core pass stages 64
+ *           samples in shared memory and holds Y in registers: it needs n x ceil4(r) <= 16384
+ *           and 64 (n + 1) elements plus n x ceil4(r) of the compute type (FP32, or FP64 for
+ *           F64 samples) within 227 KB; outside that the call returns STMF_EINVAL (for example
+ *           F64 samples with n = 512, or n = 512 with r > 32).
  *  nu       device, p FP64 positive sample weights (Sec. 3 allows any positive vector), or NULL
  *           for the paper's default nu_l = 1/p.
  *  d        tensor order, 2 <= d <= 8 (d = 2 is the matrix case).
@@ -265,7 +270,7 @@ typedef struct stmf_server* stmf_server_t;
 typedef struct {
   int32_t device;
   int32_t max_fits;      /* fit slots (concurrent starts), >= 1 */
-  int32_t n_max;         /* largest n of any request (<= 256) */
+  int32_t n_max;         /* largest n of any request (<= 512) */
   int32_t r_max;         /* largest r of any request (<= 64) */
   int32_t m_max;         /* largest L-BFGS memory of any request */
   int32_t reserved;
@@ -412,7 +417,7 @@ STMF_API stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d,
  * first call on a device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
  *
- * Limits: as for stmf_fg (n <= 256, r <= 64, 2 <= d <= 8). The pass runs at most
+ * Limits: as for stmf_fg (n <= 512, r <= 64, 2 <= d <= 8). The pass runs at most
  * floor((2^20 - r^2) / ((n + 1) r)) - 1 blocks so that every request within these limits fits the
  * scratch (a request outside them returns STMF_EINVAL before any work; STMF_ENOMEM would mean
  * the scratch cannot hold two blocks' partials, which no valid n, r reaches).

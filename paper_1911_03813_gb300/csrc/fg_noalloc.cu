@@ -59,7 +59,7 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   // argument checks (the same rules as stmf_fg)
   if (!V || !V->data) return STMF_EINVAL;
   const int eb = stmf::elem_bytes(V->dtype);
-  if (eb == 0 || V->n < 1 || V->n > 256 || V->p < 1 || V->p > (int64_t(1) << 40) ||
+  if (eb == 0 || V->n < 1 || V->n > 512 || V->p < 1 || V->p > (int64_t(1) << 40) ||
       V->ld < V->n || (V->ld * eb) % 16 != 0 ||
       (reinterpret_cast<uintptr_t>(V->data) & 15) != 0)
     return STMF_EINVAL;

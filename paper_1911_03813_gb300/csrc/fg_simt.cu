@@ -18,7 +18,7 @@
 namespace stmf {
 namespace {
 
-constexpr int TS = 64;      // samples per tile
+constexpr int TS_MAX = 64;  // samples per tile (32 when a 64-sample tile does not fit)
 constexpr int NT = 256;     // threads per block
 constexpr int MAXACC = 64;  // Y accumulators per thread
 
@@ -52,7 +52,7 @@ __device__ __forceinline__ TC ipow(TC z, int e) {
 __host__ __device__ inline int vstride_of(int n) { return (n % 2 == 0) ? n + 1 : n; }
 
 template <typename TC>
-size_t smem_bytes(int n, int rp) {
+size_t smem_bytes(int n, int rp, int TS) {
   auto up16 = [](size_t b) { return (b + 15) & ~size_t(15); };
   size_t b = up16(sizeof(TC) * size_t(n) * rp);          // As[n][rp]
   b += up16(sizeof(TC) * size_t(TS) * vstride_of(n));    // Vs[TS][vstride]
@@ -89,8 +89,9 @@ __device__ __forceinline__ double rrf_omega(int64_t l, int j, uint64_t seed) {
 
 // RRF = false: the fused pass of Alg. 2. RRF = true: the randomized range finder of eq. rrf,
 // Y_part = sum_l v_l omega_l^T with the test matrix drawn in phase 1 (no w).
-template <typename TC, int DT, int JB, bool RRF = false>
+template <typename TC, int DT, int JB, bool RRF, int TS>
 __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
+  constexpr int QG = NT / TS;  // phase 1: groups of column quads (one sample per thread)
   using TS_t = typename Storage<DT>::T;
   if (prm.skip && *prm.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -182,15 +183,15 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
         Ws[e] = (s < valid && j < r) ? (TC)rrf_omega(s0 + s, j, prm.seed) : (TC)0;
       }
     } else
-    // phase 1: z = v_s^T a_j for the thread's sample s and column quads q0, q0+4, ...
+    // phase 1: z = v_s^T a_j for the thread's sample s and column quads q0, q0 + QG, ...
     {
       const int s = tid % TS;
-      const int q0 = tid / TS;
+      const int q0 = tid / TS;  // column quads q0, q0 + QG, ...
       const TC nu_s = nus[s];
       const TC* vrow = Vs + s * vst;
 #pragma unroll
-      for (int kq = 0; kq < 4; ++kq) {
-        const int q = q0 + 4 * kq;
+      for (int kq = 0; kq < 16 / QG; ++kq) {
+        const int q = q0 + QG * kq;
         if (4 * q < rp) {
           TC z0 = 0, z1 = 0, z2 = 0, z3 = 0;
           const TC* acol = As + 4 * q;
@@ -259,44 +260,68 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
     }
   }
   __syncthreads();
-  // w_j = sum over the two warps that own column quad q0 = (j/4) % 4, slot (j/4)/4
+  // w_j = sum over the TS / 32 warps that own column quad q0 = (j/4) % QG, slot (j/4) / QG
   for (int j = tid; j < r; j += NT) {
-    const int q = j / 4, c = j % 4, q0 = q % 4, kq = q / 4;
-    part[j] = wsh[(2 * q0) * 16 + kq * 4 + c] + wsh[(2 * q0 + 1) * 16 + kq * 4 + c];
+    const int q = j / 4, c = j % 4, q0 = q % QG, kq = q / QG;
+    double t = 0.0;
+    for (int w = q0 * (TS / 32); w < (q0 + 1) * (TS / 32); ++w) t += wsh[w * 16 + kq * 4 + c];
+    part[j] = t;
   }
 }
 
-template <typename TC, int DT, int JB, bool RRF = false>
+constexpr size_t kSmemMax = 232448;
+
+// Samples per tile: 64, or 32 when a 64-sample tile of the compute type does not fit (FP64 at
+// large n). With FP32 compute and n x rp <= NT * MAXACC a 64-sample tile always fits.
+template <typename TC>
+int tile_of(int n, int rp) {
+  return smem_bytes<TC>(n, rp, TS_MAX) <= kSmemMax ? TS_MAX : TS_MAX / 2;
+}
+
+template <typename TC, int DT, int JB, bool RRF, int TS>
 cudaError_t launch_one(const FgParams& prm, int grid, cudaStream_t s) {
-  const size_t smem = smem_bytes<TC>(prm.n, prm.r_pad);
+  const size_t smem = smem_bytes<TC>(prm.n, prm.r_pad, TS);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB, RRF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB, RRF, TS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_simt_kernel<TC, DT, JB, RRF><<<grid, NT, smem, s>>>(prm);
+  fg_simt_kernel<TC, DT, JB, RRF, TS><<<grid, NT, smem, s>>>(prm);
   return cudaGetLastError();
+}
+
+template <typename TC, int DT, bool RRF, int TS>
+cudaError_t launch_ts(const FgParams& prm, int grid, cudaStream_t s) {
+  if (prm.r_pad % 16 == 0) return launch_one<TC, DT, 16, RRF, TS>(prm, grid, s);
+  if (prm.r_pad % 8 == 0) return launch_one<TC, DT, 8, RRF, TS>(prm, grid, s);
+  return launch_one<TC, DT, 4, RRF, TS>(prm, grid, s);
 }
 
 template <typename TC, int DT, bool RRF = false>
 cudaError_t launch_jb(const FgParams& prm, int grid, cudaStream_t s) {
-  if (prm.r_pad % 16 == 0) return launch_one<TC, DT, 16, RRF>(prm, grid, s);
-  if (prm.r_pad % 8 == 0) return launch_one<TC, DT, 8, RRF>(prm, grid, s);
-  return launch_one<TC, DT, 4, RRF>(prm, grid, s);
+  if constexpr (sizeof(TC) == 8) {
+    if (tile_of<TC>(prm.n, prm.r_pad) != TS_MAX)
+      return launch_ts<TC, DT, RRF, TS_MAX / 2>(prm, grid, s);
+  }
+  return launch_ts<TC, DT, RRF, TS_MAX>(prm, grid, s);
 }
 
 }  // namespace
 
 size_t fg_simt_smem(int dtype, int n, int r) {
   const int rp = (r + 3) / 4 * 4;
-  return dtype == STMF_F64 ? smem_bytes<double>(n, rp) : smem_bytes<float>(n, rp);
+  // the block's threads hold all n x rp entries of Y in registers: NT * MAXACC of them at most
+  if (size_t(n) * size_t(rp) > size_t(NT) * MAXACC) return ~size_t(0);
+  return dtype == STMF_F64 ? smem_bytes<double>(n, rp, tile_of<double>(n, rp))
+                           : smem_bytes<float>(n, rp, TS_MAX);
 }
 
 int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms) {
   const int rp = (r + 3) / 4 * 4;
-  const size_t smem = dtype == STMF_F64 ? smem_bytes<double>(n, rp) : smem_bytes<float>(n, rp);
+  const int TS = dtype == STMF_F64 ? tile_of<double>(n, rp) : TS_MAX;
+  const size_t smem = dtype == STMF_F64 ? smem_bytes<double>(n, rp, TS) : smem_bytes<float>(n, rp, TS);
   // blocks per SM bounded by shared memory (228 KB per SM) and registers (1 or 2 per SM)
   int per_sm = (int)((228 * 1024) / (smem + 1024));
   const int reg_cap = dtype == STMF_F64 ? 1 : 2;
@@ -318,16 +343,25 @@ cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_
 }
 
 int rrf_grid(int, int n, int r, int64_t p, int num_sms) {
-  return fg_simt_grid(STMF_F64, n, r, p, num_sms);  // the range finder accumulates in FP64
+  // the FP64 grid (one block per SM) serves both variants of the range finder
+  return fg_simt_grid(STMF_F64, n, r, p, num_sms);
 }
 
-cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s, bool f64) {
+  if (f64) {
+    switch (dtype) {
+      case STMF_F64: return launch_jb<double, STMF_F64, true>(prm, grid, s);
+      case STMF_F32: return launch_jb<double, STMF_F32, true>(prm, grid, s);
+      case STMF_BF16: return launch_jb<double, STMF_BF16, true>(prm, grid, s);
+      case STMF_E4M3: return launch_jb<double, STMF_E4M3, true>(prm, grid, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (dtype) {
-    case STMF_F64: return launch_jb<double, STMF_F64, true>(prm, grid, s);
-    case STMF_F32: return launch_jb<double, STMF_F32, true>(prm, grid, s);
-    case STMF_BF16: return launch_jb<double, STMF_BF16, true>(prm, grid, s);
-    case STMF_E4M3: return launch_jb<double, STMF_E4M3, true>(prm, grid, s);
-    default: return cudaErrorInvalidValue;
+    case STMF_F32: return launch_jb<float, STMF_F32, true>(prm, grid, s);
+    case STMF_BF16: return launch_jb<float, STMF_BF16, true>(prm, grid, s);
+    case STMF_E4M3: return launch_jb<float, STMF_E4M3, true>(prm, grid, s);
+    default: return cudaErrorInvalidValue;  // FP64 samples need the FP64 variant
   }
 }
 

@@ -1,7 +1,8 @@
 // ||X||^2 = nu^T (V^T V)^d nu (Lemma 3.4 applied to X, Sec. 3.3) on the CUDA cores.
 //
 // The p x p Gram matrix is never formed: persistent blocks walk the upper triangle of
-// 64 x 64 sample-tile pairs (I <= J), form the tile G = V_I V_J^T in registers, and add
+// 64 x 64 sample-tile pairs (I <= J), form the tile G = V_I V_J^T in registers (features staged
+// in chunks of at most KC, so any n fits in shared memory), and add
 // (2 - [I == J]) * sum_{l in I, k in J} nu_l nu_k G_lk^d to an FP64 block total. Block totals are
 // summed in index order by reduce_scalar (deterministic).
 #include <cuda_bf16.h>
@@ -13,6 +14,7 @@ namespace stmf {
 namespace {
 
 constexpr int TG = 64;   // samples per tile
+constexpr int KC = 128;  // features per shared-memory chunk
 constexpr int NT = 256;  // threads: 16 x 16, each a 4 x 4 block of the tile pair
 
 template <int DT> struct St;
@@ -44,15 +46,15 @@ __device__ __forceinline__ void pair_of(int64_t q, int64_t T, int64_t& I, int64_
   J = i + (q - start(i));
 }
 
+// features [k0, k0 + kc) of samples s0 .. s0 + TG (zero past `valid`), row stride gs
 template <typename TC, int DT>
 __device__ void load_tile(TC* dst, const typename St<DT>::T* V, const float* scale, int64_t s0,
-                          int valid, int n, int ld) {
-  const int gs = gstride(n);
-  for (int e = threadIdx.x; e < TG * n; e += NT) {
-    const int s = e / n, i = e - s * n;
+                          int valid, int k0, int kc, int gs, int ld) {
+  for (int e = threadIdx.x; e < TG * kc; e += NT) {
+    const int s = e / kc, i = e - s * kc;
     TC v = (TC)0;
     if (s < valid) {
-      v = cv<TC>(V[(s0 + s) * ld + i]);
+      v = cv<TC>(V[(s0 + s) * ld + k0 + i]);
       if (DT == STMF_E4M3) v *= (TC)scale[s0 + s];
     }
     dst[s * gs + i] = v;
@@ -69,7 +71,7 @@ __device__ __forceinline__ TC ipow_t(TC z, int e) {
 template <typename TC, int DT>
 __global__ void __launch_bounds__(NT) gram_simt_kernel(const GramParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = prm.n, gs = gstride(n);
+  const int n = prm.n, gs = gstride(n < KC ? n : KC);
   TC* Vi = reinterpret_cast<TC*>(smem_raw);
   TC* Vj = Vi + TG * gs;
   TC* nui = Vj + TG * gs;
@@ -85,29 +87,32 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const GramParams prm) {
     pair_of(q, T, I, J);
     const int vi = (int)(prm.p - I * TG < TG ? prm.p - I * TG : TG);
     const int vj = (int)(prm.p - J * TG < TG ? prm.p - J * TG : TG);
-    __syncthreads();
-    load_tile<TC, DT>(Vi, V, prm.scale, I * TG, vi, n, prm.ld);
-    load_tile<TC, DT>(Vj, V, prm.scale, J * TG, vj, n, prm.ld);
-    if (tid < TG) {
-      nui[tid] = tid < vi ? (TC)(prm.nu ? prm.nu[I * TG + tid] : prm.nu_uniform) : (TC)0;
-      nuj[tid] = tid < vj ? (TC)(prm.nu ? prm.nu[J * TG + tid] : prm.nu_uniform) : (TC)0;
-    }
-    __syncthreads();
     TC g[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) g[a][b] = (TC)0;
-    for (int i = 0; i < n; ++i) {
-      TC x[4], y[4];
+    for (int k0 = 0; k0 < n; k0 += KC) {  // features in index order, chunk by chunk
+      const int kc = n - k0 < KC ? n - k0 : KC;
+      __syncthreads();
+      load_tile<TC, DT>(Vi, V, prm.scale, I * TG, vi, k0, kc, gs, prm.ld);
+      load_tile<TC, DT>(Vj, V, prm.scale, J * TG, vj, k0, kc, gs, prm.ld);
+      if (k0 == 0 && tid < TG) {
+        nui[tid] = tid < vi ? (TC)(prm.nu ? prm.nu[I * TG + tid] : prm.nu_uniform) : (TC)0;
+        nuj[tid] = tid < vj ? (TC)(prm.nu ? prm.nu[J * TG + tid] : prm.nu_uniform) : (TC)0;
+      }
+      __syncthreads();
+      for (int i = 0; i < kc; ++i) {
+        TC x[4], y[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) x[a] = Vi[(4 * ty + a) * gs + i];
+        for (int a = 0; a < 4; ++a) x[a] = Vi[(4 * ty + a) * gs + i];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) y[b] = Vj[(4 * tx + b) * gs + i];
+        for (int b = 0; b < 4; ++b) y[b] = Vj[(4 * tx + b) * gs + i];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) g[a][b] += x[a] * y[b];
+          for (int b = 0; b < 4; ++b) g[a][b] += x[a] * y[b];
+      }
     }
     TC part = (TC)0;
 #pragma unroll
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(NT) gram_simt_kernel(const GramParams prm) {
 
 template <typename TC>
 size_t gram_smem(int n) {
-  return sizeof(TC) * (2 * size_t(TG) * gstride(n) + 2 * TG);
+  return sizeof(TC) * (2 * size_t(TG) * gstride(n < KC ? n : KC) + 2 * TG);
 }
 
 template <typename TC, int DT>

@@ -284,7 +284,7 @@ void stmf_server::run() {
 }
 
 extern "C" stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_server_t* out) {
-  if (!cfg || !out || cfg->max_fits < 1 || cfg->n_max < 1 || cfg->n_max > 256 || cfg->r_max < 1 ||
+  if (!cfg || !out || cfg->max_fits < 1 || cfg->n_max < 1 || cfg->n_max > 512 || cfg->r_max < 1 ||
       cfg->r_max > 64 || cfg->m_max < 1 || cfg->m_max > 64)
     return STMF_EINVAL;
   *out = nullptr;

@@ -13,6 +13,7 @@
 namespace {
 
 constexpr size_t kMaxSmem = 232448;  // dynamic shared memory per block on sm_103
+constexpr int64_t kMaxN = 512;       // features per sample
 
 stmf_status fail(stmf_ctx* c, stmf_status st, const std::string& msg) {
   if (c) c->last_error = msg;
@@ -28,7 +29,7 @@ stmf_status check_samples(stmf_ctx* c, const stmf_samples* V) {
   if (!V->data) return fail(c, STMF_EINVAL, "V->data is NULL");
   const int eb = stmf::elem_bytes(V->dtype);
   if (eb == 0) return fail(c, STMF_EINVAL, "V->dtype is not a stmf_dtype");
-  if (V->n < 1 || V->n > 256) return fail(c, STMF_EINVAL, "V->n must be in [1, 256]");
+  if (V->n < 1 || V->n > kMaxN) return fail(c, STMF_EINVAL, "V->n must be in [1, 512]");
   if (V->p < 1) return fail(c, STMF_EINVAL, "V->p must be >= 1");
   if (V->p > (int64_t(1) << 40)) return fail(c, STMF_EINVAL, "V->p is too large");
   if (V->ld < V->n) return fail(c, STMF_EINVAL, "V->ld must be >= V->n");
@@ -309,7 +310,10 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   if (r_hat < 1 || r_hat > 64) return fail(c, STMF_EINVAL, "r_hat must be in [1, 64]");
   if (!A0) return fail(c, STMF_EINVAL, "A0 is NULL");
   const int n = (int)V->n;
-  if (stmf::fg_simt_smem(STMF_F64, n, (int)r_hat) > kMaxSmem)
+  // FP64 products and sums while a 64-sample FP64 tile fits in shared memory; beyond that (large
+  // n) FP32 products with FP32 sums over 16 tiles folded into FP64
+  const bool f64 = stmf::fg_simt_smem(STMF_F64, n, (int)r_hat) <= kMaxSmem;
+  if (!f64 && stmf::fg_simt_smem(STMF_F32, n, (int)r_hat) > kMaxSmem)
     return fail(c, STMF_EINVAL, "n * r_hat too large for the range finder (shared memory)");
   const int grid = stmf::rrf_grid(V->dtype, n, (int)r_hat, V->p, c->num_sms);
   const size_t L = size_t(r_hat) + size_t(n) * size_t(r_hat);
@@ -328,10 +332,10 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   prm.d = 2;
   prm.r = (int)r_hat;
   prm.r_pad = (int)((r_hat + 3) / 4 * 4);
-  prm.flush_tiles = 1 << 30;  // FP64 accumulators: no intermediate folds needed
+  prm.flush_tiles = f64 ? 1 << 30 : 16;  // FP64 accumulators need no intermediate folds
   prm.status = c->status;
   prm.seed = seed;
-  cudaError_t e = stmf::rrf_launch(V->dtype, prm, grid, s);
+  cudaError_t e = stmf::rrf_launch(V->dtype, prm, grid, s, f64);
   if (e != cudaSuccess) return cuda_fail(c, e, "range finder launch");
   stmf::ModelParams mp{};
   mp.partials = partials;
@@ -364,7 +368,7 @@ stmf_status stmf_fg_finish(stmf_ctx_t c, const double* yw, int64_t n, int32_t d,
   if (!c) return STMF_EINVAL;
   if (!yw || !lambda || !A || !f || !g_lambda || !G_A)
     return fail(c, STMF_EINVAL, "NULL argument");
-  if (n < 1 || n > 256 || r < 1 || r > 64 || d < 2 || d > 8)
+  if (n < 1 || n > kMaxN || r < 1 || r > 64 || d < 2 || d > 8)
     return fail(c, STMF_EINVAL, "n, r or d out of range");
   stmf_status st = ensure_ws(c, size_t(r) * size_t(r) * sizeof(double));
   if (st != STMF_OK) return st;
@@ -393,7 +397,7 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   if (!V || !V->data || !lambda || !A || !f || !g_lambda || !G_A)
     return fail(c, STMF_EINVAL, "NULL argument");
   const int eb = stmf::elem_bytes(V->dtype);
-  if (eb == 0 || V->n < 1 || V->n > 256 || V->p < 1 || V->ld < V->n || (V->ld * eb) % 16 != 0)
+  if (eb == 0 || V->n < 1 || V->n > kMaxN || V->p < 1 || V->ld < V->n || (V->ld * eb) % 16 != 0)
     return fail(c, STMF_EINVAL, "invalid samples");
   if ((V->dtype == STMF_E4M3) != (V->scale != nullptr))
     return fail(c, STMF_EINVAL, "E4M3 samples need scales (and only they)");
@@ -534,8 +538,6 @@ stmf_status stmf_norm_x(stmf_ctx_t c, const stmf_samples* V, const double* nu, i
   if (st != STMF_OK) return st;
   if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
   if (!alpha_out) return fail(c, STMF_EINVAL, "alpha_out is NULL");
-  if (V->dtype == STMF_F64 && V->n > 200)
-    return fail(c, STMF_EINVAL, "FP64 samples: n must be <= 200 for the Gram pass");
   const bool tc = stmf::gram_tc_supported(V->dtype, (int)V->n, V->p);
   const int grid = tc ? stmf::gram_tc_grid(V->p, c->num_sms)
                       : stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);

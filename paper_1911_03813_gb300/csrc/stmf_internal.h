@@ -60,12 +60,15 @@ struct GramParams {
 
 // Host launchers, one per translation unit. Each returns cudaSuccess or the launch error.
 // `grid_out` receives the grid size used (partials has grid_out slots).
-size_t fg_simt_smem(int dtype, int n, int r);  // dynamic shared memory of the pass
+// dynamic shared memory of the pass; SIZE_MAX when n x r does not fit the block's registers
+size_t fg_simt_smem(int dtype, int n, int r);
 int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 // Randomized range finder (eq. rrf): block partials of V Omega into prm.partials (w part zero).
+// f64: FP64 products and sums (needs fg_simt_smem(STMF_F64, n, r) <= 232448), else FP32 products
+// with FP32 sums folded into FP64 every prm.flush_tiles tiles.
 int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms);
-cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s, bool f64);
 // Sum the block partials only (no model terms): yw = sum_g partials[g].
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
 // Alg. 2 lines 4-9 from a given yw = [w; vec(Y)] (B = A^T A, then the outputs).

@@ -302,3 +302,22 @@ def test_fg_near_fit(stmf, dtype, sigma):
     assert ef <= 1e-6 and eg <= 1e-5 and eG <= 1e-5, (ef, eg, eG)
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("d", [3, 4])
+def test_fg_e4m3_every_code(stmf, d):
+    """Every finite E4M3 code (normals, subnormals, both zeros) goes through the tensor-core
+    pass's widening to BF16: each sample holds all 254 finite codes in a seeded order, with
+    seeded per-sample scales."""
+    n, p, r = 254, 1000, 16
+    codes = np.array([c for c in range(256) if c not in (0x7F, 0xFF)], dtype=np.uint8)
+    g = inputs.rng(254)
+    q = np.stack([g.permutation(codes) for _ in range(p)])
+    ld = inputs.padded_ld(n, "e4m3")
+    bits = np.zeros((p, ld), dtype=np.uint8)
+    bits[:, :n] = q
+    scale = np.exp2(g.uniform(-12.0, -6.0, p)).astype(np.float32)
+    st = dict(data=torch.from_numpy(bits).view(torch.float8_e4m3fn).cuda(),
+              scale=torch.from_numpy(scale).cuda(), n=n, ld=ld, dtype="e4m3")
+    lam, A = inputs.random_model(n, r, seed=255)
+    check_fg(stmf, st, None, lam, A, d, TOL["e4m3"])
