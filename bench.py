@@ -279,7 +279,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=P_FULL)
     ap.add_argument("--serving-requests", type=int, default=256)
@@ -401,9 +401,12 @@ def main():
         for _ in range(2):
             stmf.fg_host(st_h, None, D, lam_h, A_h)
         barrier()
+        calls = []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            tc = time.perf_counter()
             stmf.fg_host(st_h, None, D, lam_h, A_h)
+            calls.append(time.perf_counter() - tc)
         el = time.perf_counter() - t0
         barrier()
         # the host-to-device link's own copy rate (one pinned 1 GiB copy, CUDA events): the
@@ -425,6 +428,8 @@ def main():
                "link_frac": round(h2d_gbs / link_gbs, 3),
                "h2d_bytes_per_step": bytes16 + 8 * (R + R * N_FEAT + 1),
                "d2h_bytes_per_step": 8 * (1 + R + R * N_FEAT),
+               "call_ms_median": round(1e3 * statistics.median(calls), 2),
+               "call_ms_min": round(1e3 * min(calls), 2),
                "call": "stmf_fg_host (pinned host V, chunked H2D overlapped with the passes)"}
         del host16, st_h
 

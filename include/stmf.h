@@ -147,7 +147,7 @@ STMF_API stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double
 /*
  * stmf_fg_host -- stmf_fg with every array in HOST memory (the end-to-end call). V (and nu, the
  * E4M3 scales) are streamed to the device in chunks of about 256 MB through three library-owned
- * staging buffers on two copy streams, so the copy of one chunk overlaps the pass over the
+ * staging buffers on one copy stream, so the copy of one chunk overlaps the pass over the
  * previous ones; chunk partials are summed in FP64 in chunk order; f, g_lambda and G_A are
  * copied back. Use pinned host memory for V: from pageable memory the copies do not overlap.
  *  V        host samples (stmf_samples with host pointers).   nu  host p FP64 or NULL (1/p).

@@ -457,12 +457,12 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   cudaMemcpyAsync(d_A, A, sizeof(double) * n * r, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(d_alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s);
   cudaEvent_t start_ev = c->copied[2];
-  cudaEventRecord(start_ev, s);  // the copy streams start after the previous work on `s`
-  for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(c->copy_stream[k], start_ev, 0);
+  cudaEventRecord(start_ev, s);  // the copies start after the previous work on `s`
+  cudaStreamWaitEvent(c->copy_stream[0], start_ev, 0);
   const int64_t nchunks = (p + rows - 1) / rows;
   for (int64_t ch = 0; ch < nchunks; ++ch) {
     const int k = int(ch % 3);
-    cudaStream_t cs = c->copy_stream[ch % 2];
+    cudaStream_t cs = c->copy_stream[0];  // one stream: chunk copies in order at the link rate
     const int64_t lo = ch * rows, cnt = (lo + rows <= p) ? rows : p - lo;
     unsigned char* buf = static_cast<unsigned char*>(c->stage[k]);
     if (ch >= 3) cudaStreamWaitEvent(cs, c->consumed[k], 0);  // the pass over chunk ch-3 is done
