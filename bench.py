@@ -238,6 +238,35 @@ def gram_bench(dev):
             "flop_counted": "2*128*128*n per computed 128x128 tile pair, upper triangle"}
 
 
+def alpha_bench(dev):
+    """||X||^2 at the FP32 scale workload (n=100, p=2.5e6, 10 means, d=3): the method stmf_norm_x
+    picks (the distinct entries of the symmetric X) against the Gram form, whose time is
+    extrapolated from a 2^16-sample slice by (p / 2^16)^2."""
+    import torch
+
+    from paper_1911_03813_gb300 import inputs, stmf
+    n, p, d = 100, 2500000, 3
+    st = inputs.gmm_device(n, p, 10, 0.1, SEED + 7, dev, out_dtype="f32")
+    stmf.norm_x(st, None, d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = stmf.norm_x(st, None, d)
+    torch.cuda.synchronize()
+    t_auto = time.perf_counter() - t0
+    sl = dict(st)
+    sl["data"] = st["data"][: 1 << 16]
+    stmf.norm_x(sl, None, d, method="gram")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stmf.norm_x(sl, None, d, method="gram")
+    torch.cuda.synchronize()
+    t_gram = (time.perf_counter() - t0) * (p / (1 << 16)) ** 2
+    del st, sl
+    return {"n": n, "p": p, "d": d, "dtype": "f32", "method": "compressed symmetric X",
+            "s": t_auto, "gram_s_extrapolated": t_gram, "speedup": t_gram / t_auto,
+            "alpha": a.item()}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -451,6 +480,7 @@ def main():
     del st16, st32, st8
     torch.cuda.empty_cache()
     gram = None if args.no_gram else gram_bench(dev)
+    alpha = None if args.no_gram else alpha_bench(dev)
     serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = ncu_traffic("fg_pass_bf16")
@@ -481,6 +511,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "e2e": e2e,
         "gram": gram,
+        "alpha_fp32_scale": alpha,
         "serving": serving,
         "cpu_baseline": cpu,
     }

@@ -184,14 +184,28 @@ STMF_API stmf_status stmf_fg_finish(stmf_ctx_t ctx, const double* yw, int64_t n,
                                     stmf_stream_t stream);
 
 /*
- * stmf_norm_x -- alpha = ||X||^2 = nu^T (V^T V)^d nu, Lemma 3.4 applied to X (Sec. 3.3), the
- * O(n p^2) constant of Alg. 2. Evaluated over the upper triangle of sample-tile pairs without
- * forming the p x p Gram matrix; per-tile sums are combined in FP64.
+ * stmf_norm_x -- alpha = ||X||^2, the constant of Alg. 2 (Sec. 3.3), by the cheaper of the two
+ * methods of stmf_norm_x_method (method 0).
+ *
+ * stmf_norm_x_method -- alpha = ||X||^2 by a chosen method:
+ *  1  the Gram form nu^T (V^T V)^d nu (Lemma 3.4 applied to X), n p^2 / 2 multiply-adds, over
+ *     the upper triangle of sample-tile pairs without forming the p x p Gram matrix;
+ *  2  the distinct entries of the symmetric X (Sec. 3.3 notes that forming X can be cheaper than
+ *     the implicit O(n p^2) route): X_m = sum_l nu_l prod_{i in m} v_li for every multiset m of
+ *     d features and ||X||^2 = sum_m (d! / prod of the multiplicities' factorials) X_m^2, about
+ *     p C(n+d-1, d) multiply-adds; needs C(n+d-2, d-1) <= 2^22 and, for FP64 samples, n <= 512
+ *     (the first call for an (n, d) builds a prefix table and synchronises the device);
+ *  0  the cheaper of the two by their operation counts.
+ * Per-block sums are combined in FP64 in a fixed order (reproducible bit for bit).
  *  V, nu, d   as for stmf_fg.     alpha_out  device, 1 FP64 (out).
- * Enqueued on `stream`; asynchronous.
+ * Enqueued on `stream`; asynchronous. STMF_EINVAL for an unknown method or a method-2 request
+ * past its limits.
  */
 STMF_API stmf_status stmf_norm_x(stmf_ctx_t ctx, const stmf_samples* V, const double* nu, int32_t d,
                         double* alpha_out, stmf_stream_t stream);
+STMF_API stmf_status stmf_norm_x_method(stmf_ctx_t ctx, const stmf_samples* V, const double* nu,
+                                        int32_t d, int32_t method, double* alpha_out,
+                                        stmf_stream_t stream);
 
 /*
  * Kernel timing for benchmarks (not part of the method). While enabled, every stmf_fg records

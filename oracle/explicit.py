@@ -103,3 +103,21 @@ def fg_explicit(X, lam, A, alpha=0.0):
     g_lam = -2.0 * (w - u)                  # line 8
     G_A = -2.0 * d * (Y - A @ np.diag(lam) @ C) @ np.diag(lam)   # line 9
     return float(f), g_lam, G_A
+
+
+def norm_x_explicit(nu, V, d, chunk=4096):
+    """||X||^2 = <X, X> with X = sum_l nu_l v_l^{(x)d} formed explicitly (eq. tensorX), as the
+    n^(d-1) x n matrix sum_l nu_l vec(v_l^{(x)(d-1)}) v_l^T accumulated over chunks of samples
+    (V: n x p; nu: p weights or None for 1/p). Memory n^d; for d up to 4 at moderate n."""
+    V = np.asarray(V, dtype=np.float64)
+    n, p = V.shape
+    w = np.full(p, 1.0 / p) if nu is None else np.asarray(nu, dtype=np.float64)
+    X = np.zeros((n ** (d - 1), n))
+    for c0 in range(0, p, chunk):
+        c1 = min(p, c0 + chunk)
+        Vc = V[:, c0:c1].T                      # samples x n
+        K = Vc.copy()
+        for _ in range(d - 2):                  # rows: v^{(x)(d-1)} flattened
+            K = (K[:, :, None] * Vc[:, None, :]).reshape(c1 - c0, -1)
+        X += K.T @ (w[c0:c1, None] * Vc)
+    return float(np.sum(X * X))

@@ -251,6 +251,7 @@ stmf_status stmf_destroy(stmf_ctx_t c) {
   for (int k = 0; k < 2; ++k)
     if (c->copy_stream[k]) cudaStreamDestroy(c->copy_stream[k]);
   if (c->host_small) cudaFree(c->host_small);
+  if (c->sym_dev) cudaFree(c->sym_dev);
   delete c;
   return STMF_OK;
 }
@@ -440,6 +441,7 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   const size_t small = sizeof(double) * (r + n * r + 1 + L + 1 + r + n * r);
   if (small > c->host_small_bytes) {
     if (c->host_small) cudaFree(c->host_small);
+  if (c->sym_dev) cudaFree(c->sym_dev);
     c->host_small = nullptr;
     c->host_small_bytes = 0;
     if (cudaMalloc(&c->host_small, small) != cudaSuccess)
@@ -531,13 +533,90 @@ stmf_status stmf_profile_read(stmf_ctx_t c, double* total_ms, int64_t* count) {
   return STMF_OK;
 }
 
+namespace {
+constexpr double kMaxSymPrefixes = double(1 << 22);  // prefix table of at most 96 MB
+
+// ||X||^2 from the distinct entries of the symmetric moment tensor (norm_sym.cu)
+stmf_status norm_x_sym(stmf_ctx* c, const stmf_samples* V, const double* nu, int d,
+                       double* alpha_out, cudaStream_t s) {
+  const int n = (int)V->n;
+  if (stmf::sym_prefix_count(n, d) > kMaxSymPrefixes)
+    return fail(c, STMF_EINVAL, "C(n + d - 2, d - 1) too large for the compressed tensor");
+  if (stmf::norm_sym_smem(V->dtype, n) > kMaxSmem - 1024)
+    return fail(c, STMF_EINVAL, "n too large for the compressed tensor (shared memory)");
+  if (c->sym_n != n || c->sym_d != d || !c->sym_dev) {
+    std::vector<stmf::SymPrefix> tab;
+    stmf::sym_prefixes(n, d, tab);
+    const size_t bytes = tab.size() * sizeof(stmf::SymPrefix);
+    // an earlier call may still read the old table
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize (prefix table)");
+    if (bytes > c->sym_dev_bytes) {
+      if (c->sym_dev) cudaFree(c->sym_dev);
+      c->sym_dev = nullptr;
+      c->sym_dev_bytes = 0;
+      if (cudaMalloc(&c->sym_dev, bytes) != cudaSuccess)
+        return fail(c, STMF_ENOMEM, "cudaMalloc of the prefix table failed");
+      c->sym_dev_bytes = bytes;
+    }
+    e = cudaMemcpy(c->sym_dev, tab.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prefix table upload");
+    c->sym_n = n;
+    c->sym_d = d;
+    c->sym_count = (long long)tab.size();
+  }
+  const dim3 grid = stmf::norm_sym_grid(c->sym_count, n, V->p, c->num_sms);
+  const size_t slab_bytes = stmf::norm_sym_slab_bytes(c->sym_count, grid);
+  const int nblk = stmf::norm_sym_square_blocks(c->sym_count);
+  stmf_status st = ensure_ws(c, slab_bytes + size_t(nblk) * sizeof(double));
+  if (st != STMF_OK) return st;
+  stmf::SymParams sp{};
+  sp.V = V->data;
+  sp.scale = V->scale;
+  sp.nu = nu;
+  sp.nu_uniform = 1.0 / double(V->p);
+  sp.prefixes = static_cast<const stmf::SymPrefix*>(c->sym_dev);
+  sp.count = c->sym_count;
+  sp.slabs = static_cast<double*>(c->ws);
+  sp.partials = sp.slabs + slab_bytes / sizeof(double);
+  sp.p = V->p;
+  sp.n = n;
+  sp.ld = (int)V->ld;
+  sp.d = d;
+  cudaError_t e = stmf::norm_sym_launch(V->dtype, sp, grid, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "compressed tensor launch");
+  e = stmf::reduce_scalar_launch(sp.partials, nblk, alpha_out, c->status, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "compressed tensor reduction launch");
+  return STMF_OK;
+}
+}  // namespace
+
 stmf_status stmf_norm_x(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32_t d,
                         double* alpha_out, stmf_stream_t stream) {
+  return stmf_norm_x_method(c, V, nu, d, 0, alpha_out, stream);
+}
+
+stmf_status stmf_norm_x_method(stmf_ctx_t c, const stmf_samples* V, const double* nu, int32_t d,
+                               int32_t method, double* alpha_out, stmf_stream_t stream) {
   if (!c) return STMF_EINVAL;
   stmf_status st = check_samples(c, V);
   if (st != STMF_OK) return st;
   if (d < 2 || d > 8) return fail(c, STMF_EINVAL, "d must be in [2, 8]");
   if (!alpha_out) return fail(c, STMF_EINVAL, "alpha_out is NULL");
+  if (method < 0 || method > 2) return fail(c, STMF_EINVAL, "method must be 0, 1 or 2");
+  if (method == 0) {
+    // multiply-adds of each form: the compressed tensor ~ prefixes x ceil64(n) x p, the Gram
+    // ~ n p^2 / 2; the tensor-core Gram (BF16) runs ~25x the CUDA-core rate
+    const double pre = stmf::sym_prefix_count((int)V->n, d);
+    const double cs = pre * double((V->n + 63) / 64 * 64) * double(V->p);
+    const double cg = double(V->n) * double(V->p) * double(V->p) / 2.0;
+    const bool tcg = stmf::gram_tc_supported(V->dtype, (int)V->n, V->p);
+    method = (pre <= kMaxSymPrefixes && cs * (tcg ? 25.0 : 1.0) < cg &&
+              stmf::norm_sym_smem(V->dtype, (int)V->n) <= kMaxSmem - 1024)
+                 ? 2 : 1;
+  }
+  if (method == 2)
+    return norm_x_sym(c, V, nu, d, alpha_out, reinterpret_cast<cudaStream_t>(stream));
   const bool tc = stmf::gram_tc_supported(V->dtype, (int)V->n, V->p);
   const int grid = tc ? stmf::gram_tc_grid(V->p, c->num_sms)
                       : stmf::gram_simt_grid(V->dtype, (int)V->n, V->p, c->num_sms);

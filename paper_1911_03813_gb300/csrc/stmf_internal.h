@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "stmf.h"
 
@@ -58,6 +59,27 @@ struct GramParams {
   int32_t* status;
 };
 
+// One sorted prefix of d - 1 features of the compressed symmetric moment tensor (norm_sym.cu):
+// its feature indices, the length of its last run of equal indices, and d! / prod(run lengths!).
+struct SymPrefix {
+  uint16_t idx[7];
+  uint16_t run;
+  double base;
+};
+
+struct SymParams {
+  const void* V;
+  const float* scale;
+  const double* nu;
+  double nu_uniform;
+  const SymPrefix* prefixes;  // [count], lexicographic
+  long long count;
+  double* slabs;     // [grid.z][count][grid.y * 64]: FP64 partial X per sample range
+  double* partials;  // [blocks of the squaring kernel]
+  int64_t p;
+  int n, ld, d;
+};
+
 // Host launchers, one per translation unit. Each returns cudaSuccess or the launch error.
 // `grid_out` receives the grid size used (partials has grid_out slots).
 // dynamic shared memory of the pass; SIZE_MAX when n x r does not fit the block's registers
@@ -88,6 +110,14 @@ cudaError_t gram_tc_launch(const GramParams& prm, int grid, cudaStream_t s);
 cudaError_t gram_simt_launch(int dtype, const GramParams& prm, int grid, cudaStream_t s);
 cudaError_t reduce_scalar_launch(const double* partials, int count, double* out,
                                  int32_t* status, cudaStream_t s);
+// ||X||^2 from the distinct entries of the symmetric moment tensor (norm_sym.cu).
+double sym_prefix_count(int n, int d);
+void sym_prefixes(int n, int d, std::vector<SymPrefix>& out);
+size_t norm_sym_smem(int dtype, int n);
+dim3 norm_sym_grid(long long count, int n, int64_t p, int num_sms);
+size_t norm_sym_slab_bytes(long long count, dim3 grid);
+int norm_sym_square_blocks(long long count);
+cudaError_t norm_sym_launch(int dtype, const SymParams& prm, dim3 grid, cudaStream_t s);
 
 inline int elem_bytes(int dtype) {
   switch (dtype) {
@@ -124,6 +154,11 @@ struct stmf_ctx {
   cudaEvent_t consumed[3] = {nullptr, nullptr, nullptr};
   void* host_small = nullptr;  // device: lambda, A, alpha, yw, outputs
   size_t host_small_bytes = 0;
+  // prefix table of the compressed symmetric ||X||^2 for (sym_n, sym_d)
+  void* sym_dev = nullptr;
+  size_t sym_dev_bytes = 0;
+  int sym_n = 0, sym_d = 0;
+  long long sym_count = 0;
 };
 
 namespace stmf {

@@ -65,6 +65,8 @@ def lib():
         L.stmf_fg.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, i64, dp, dp, dp, dp, dp, dp,
                               vp]
         L.stmf_norm_x.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, dp, vp]
+        L.stmf_norm_x_method.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, i32, dp, vp]
+        L.stmf_norm_x_method.restype = ctypes.c_int
         L.stmf_profile_enable.argtypes = [vp, i32]
         L.stmf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i64)]
@@ -212,17 +214,22 @@ def fg(V, nu, d, lam, A, alpha=None, out=None, stream=None, ctx=None):
     return f, gl, GA
 
 
-def norm_x(V, nu, d, out=None, stream=None, ctx=None):
-    """alpha = ||X||^2 = nu^T (V^T V)^d nu (stmf_norm_x). Returns a (1,) float64 CUDA tensor."""
+NORM_X_METHODS = {"auto": 0, "gram": 1, "compressed": 2}
+
+
+def norm_x(V, nu, d, out=None, stream=None, ctx=None, method="auto"):
+    """alpha = ||X||^2 (stmf_norm_x_method): method "gram" = nu^T (V^T V)^d nu, "compressed" =
+    from the distinct entries of the symmetric X, "auto" = the cheaper. Returns a (1,) float64
+    CUDA tensor."""
     ctx = ctx or default_context()
     desc, keep = as_samples(V)
     if nu is not None:
         _check_f64(nu, (desc.p,), "nu")
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=torch.device("cuda", ctx.device))
-    st = lib().stmf_norm_x(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d), _ptr(out),
-                           _stream(stream))
-    ctx.check(st, "stmf_norm_x")
+    st = lib().stmf_norm_x_method(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d),
+                                  NORM_X_METHODS[method], _ptr(out), _stream(stream))
+    ctx.check(st, "stmf_norm_x_method")
     del keep
     return out
 

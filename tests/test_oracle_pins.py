@@ -380,3 +380,16 @@ def test_rrf_start_in_range_of_samples():
     assert np.linalg.norm(A0 - Q @ (Q.T @ A0)) < 1e-12
     B = V @ Om
     np.testing.assert_allclose(A0 * np.linalg.norm(B, axis=0), B, rtol=1e-13)
+
+
+@pytest.mark.parametrize("n,p,d", [(3, 7, 2), (4, 9, 3), (3, 11, 4), (5, 40, 3), (6, 25, 4)])
+def test_norm_x_explicit_pins(n, p, d):
+    """||X||^2 from the explicitly formed X (chunked) equals brute force <X, X> and the Gram form
+    of Lemma 3.4 (two routes that share no arithmetic)."""
+    g = np.random.default_rng(1000 * n + p + d)
+    V = g.standard_normal((n, p))
+    nu = g.uniform(0.1, 1.0, p)
+    Xb = ex.moment_tensor(nu, V, d)
+    ref = ex.inner(Xb, Xb)
+    assert ex.norm_x_explicit(nu, V, d, chunk=4) == pytest.approx(ref, rel=1e-12)
+    assert im.norm_x(nu, V, d) == pytest.approx(ref, rel=1e-12)
