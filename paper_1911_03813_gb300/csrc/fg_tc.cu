@@ -44,7 +44,6 @@ constexpr int NEPI = 128 * EG;         // epilogue threads
 constexpr int NTHREADS = 96 + NEPI;    // producer warp, MMA1 warp, MMA2 warp, epilogue
 constexpr int NCONV = 4;               // FP8 samples: warps that widen E4M3 tiles to BF16
 constexpr int NTHREADS_FP8 = NTHREADS + 32 * NCONV;
-constexpr int Q_BYTES = TM * 128;      // one 128-feature region of an E4M3 tile (16 KB)
 // Z accumulators per tile: MMA1's K steps are split ZC ways and the partial products summed in
 // the epilogue with round-to-nearest. The tensor cores' FP32 accumulation truncates, so a long
 // run of accumulations biases |z| low (measured at n = 256: 1.6e-6 relative with one
@@ -61,7 +60,6 @@ struct TcExtra {
   int tmem_cols;
   int smem_bytes;
   int nq;         // E4M3 samples: 128-feature regions per tile (ceil(n / 128))
-  int qstages;    // E4M3 samples: TMA ring depth of E4M3 tiles
   int kpz;        // K steps (16 features each) per Z accumulator (ZC accumulators per tile)
 };
 
@@ -91,6 +89,15 @@ __device__ __forceinline__ float ipow_f(float z, int e) {
   return t;
 }
 
+// Two E4M3 codes -> two BF16 values, exactly (E4M3 -> FP16 -> FP32 -> BF16; every E4M3 value
+// has at most 4 significant bits and an exponent in -9..8, so no step rounds).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint16_t q) {
+  const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)q, __NV_E4M3);
+  const __half2 hh = *reinterpret_cast<const __half2*>(&hr);
+  const __nv_bfloat162 bb = __floats2bfloat162_rn(__low2float(hh), __high2float(hh));
+  return *reinterpret_cast<const uint32_t*>(&bb);
+}
+
 template <int C>
 __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
   if constexpr (C == 8) {
@@ -104,10 +111,12 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 }
 
 // FP8 = false: BF16 samples, TMA fills the S-stage ring the MMAs read.
-// FP8 = true:  E4M3 samples (v = s q), TMA fills a ring of E4M3 tiles, NCONV converter warps widen
-//              each tile into one of two BF16 buffers (S = 2) that the MMAs read (every E4M3 value
-//              is exactly a BF16 value), and the scale folds into the weight, nu' = nu s^d: with
-//              z = q^T a, the terms of eq. Y and Lemma 3.5 are nu' z^{d-1} q and nu' z^d.
+// FP8 = true:  E4M3 samples (v = s q): TMA brings each 128-feature half of an E4M3 tile (16 KB)
+//              into the upper 64-feature region of its two BF16 regions in the same S-stage ring,
+//              and NCONV converter warps widen it to BF16 in place (every E4M3 value is exactly a
+//              BF16 value) before the MMAs read the stage; the scale folds into the weight,
+//              nu' = nu s^d: with z = q^T a, the terms of eq. Y and Lemma 3.5 are nu' z^{d-1} q
+//              and nu' z^d.
 template <int RP, bool FP8>
 __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
@@ -126,12 +135,12 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   unsigned char* sV = base;
   unsigned char* sW = sV + size_t(S) * stage_bytes;
   unsigned char* sA = sW + 2 * 2 * C::W_REG;
-  unsigned char* sQ = sA + size_t(nreg) * C::A_REG;  // E4M3 ring (FP8 only)
-  const int QS = FP8 ? ex.qstages : 0, nq = ex.nq;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + size_t(QS) * nq * Q_BYTES);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + S;
-  uint64_t* zfull = bars + 2 * S;
+  const int nq = ex.nq;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nreg) * C::A_REG);
+  uint64_t* full = bars;          // TMA landed
+  uint64_t* empty = bars + S;     // MMA2 done with the stage
+  uint64_t* conv = bars + 2 * S;  // E4M3 samples: the stage is widened to BF16
+  uint64_t* zfull = bars + 3 * S;
   uint64_t* zempty = zfull + 2;
   uint64_t* wfull = zempty + 2;
   uint64_t* wempty = wfull + 2;
@@ -141,19 +150,14 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   double* wred = reinterpret_cast<double*>(mma_done + 3);  // 4 x RP
-  uint64_t* qfull = reinterpret_cast<uint64_t*>(wred + 4 * RP);  // FP8 only
-  uint64_t* qempty = qfull + QS;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], FP8 ? NCONV : 1);  // TMA arrival, or one per converter warp
+      tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
-    }
-    for (int s = 0; s < QS; ++s) {
-      tc::mbar_init(&qfull[s], 1);
-      tc::mbar_init(&qempty[s], NCONV);
+      tc::mbar_init(&conv[s], NCONV);  // one arrival per converter warp
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&zfull[b], 1);
@@ -214,11 +218,11 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      // BF16: tiles go straight into the MMA ring; E4M3: into the E4M3 ring for the converters
-      const int R = FP8 ? QS : S;
-      uint64_t* rfull = FP8 ? qfull : full;
-      uint64_t* rempty = FP8 ? qempty : empty;
-      const uint32_t rbytes = FP8 ? uint32_t(nq) * Q_BYTES : uint32_t(nload) * REG_BYTES;
+      // BF16: tiles go straight to the MMAs; E4M3: the converters widen them in place first
+      const int R = S;
+      uint64_t* rfull = full;
+      uint64_t* rempty = empty;
+      const uint32_t rbytes = FP8 ? uint32_t(nq) * REG_BYTES : uint32_t(nload) * REG_BYTES;
       int issued = 0;
       for (int it = 0; it < my_tiles; ++it) {
         const int st = it % R;
@@ -230,9 +234,9 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         tc::mbar_arrive_expect_tx(&rfull[st], rbytes);
         const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
         if constexpr (FP8) {
-          for (int g = 0; g < nq; ++g)
-            tc::tma_load_2d(sQ + (size_t(st) * nq + g) * Q_BYTES, &tmap, g * 128,
-                            (int32_t)(tile * TM), &rfull[st]);
+          for (int g = 0; g < nq; ++g)  // half g into BF16 region 2g + 1
+            tc::tma_load_2d(sV + size_t(st) * stage_bytes + size_t(2 * g + 1) * REG_BYTES, &tmap,
+                            g * 128, (int32_t)(tile * TM), &rfull[st]);
         } else {
           for (int g = 0; g < nload; ++g)
             tc::tma_load_2d(sV + size_t(st) * stage_bytes + size_t(g) * REG_BYTES, &tmap, g * 64,
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       bool ok = true;
       for (int t = 0; t < my_tiles; ++t) {
         const int st = t % S, zb = t & 1;
-        ok = tc::mbar_wait(&full[st], (t / S) & 1, abortv, WAIT_LIMIT) &&
+        ok = tc::mbar_wait(FP8 ? &conv[st] : &full[st], (t / S) & 1, abortv, WAIT_LIMIT) &&
              tc::mbar_wait(&zempty[zb], ((t >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
         if (!ok) break;
         tc::tc_fence_after();
@@ -322,49 +326,51 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     // 2g and 2g + 1 of MMA buffer t % 2, both in the 128-byte swizzle. Features beyond n are zero
     // (TMA fills them), so the BF16 padding is zero too.
     if constexpr (FP8) {
+      // thread ct owns row y = ct of every tile (128 converter threads, 128 samples per tile).
+      // Per 128-feature half g: the E4M3 row (128 bytes, 16-byte chunk c at position c ^ (y & 7))
+      // sits in BF16 region 2g + 1; all 8 chunks are read first, then features 0-63 become row y
+      // of region 2g and features 64-127 overwrite row y of region 2g + 1 in place. Only this
+      // thread touches row y, so nothing else can read the bytes it overwrites.
       const int ct = tid - (96 + NEPI);
-      const int chunks = nq * TM * 8;  // 16-byte chunks per E4M3 tile
+      const int y = ct;
       bool ok = true;
       for (int it = 0; it < my_tiles; ++it) {
-        const int qs = it % QS, b = it % S;
-        if (!tc::mbar_wait(&qfull[qs], (it / QS) & 1, abortv, WAIT_LIMIT) ||
-            !tc::mbar_wait(&empty[b], ((it / S) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+        const int st = it % S;
+        if (!tc::mbar_wait(&full[st], (it / S) & 1, abortv, WAIT_LIMIT)) {
           ok = false;
           break;
         }
-        const unsigned char* src = sQ + size_t(qs) * nq * Q_BYTES;
-        unsigned char* dst = sV + size_t(b) * stage_bytes;
-        for (int e = ct; e < chunks; e += 32 * NCONV) {
-          const int g = e >> 10, y = (e >> 3) & 127, c8 = e & 7;
-          const uint4 raw = *reinterpret_cast<const uint4*>(
-              src + size_t(g) * Q_BYTES + y * 128 + (((c8 ^ (y & 7)) & 7) << 4));
-          const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-          uint32_t outw[8];
+        unsigned char* stg = sV + size_t(st) * stage_bytes;
+        for (int g = 0; g < nq; ++g) {
+          unsigned char* lo = stg + size_t(2 * g) * REG_BYTES + y * 128;
+          unsigned char* hi = lo + REG_BYTES;  // holds the E4M3 row, becomes features 64-127
+          uint4 raw[8];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int c = 0; c < 8; ++c)
+            raw[c] = *reinterpret_cast<const uint4*>(hi + (((c ^ (y & 7)) & 7) << 4));
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(
-                  (__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
-              const __half2 hh = *reinterpret_cast<const __half2*>(&hr);
-              const __nv_bfloat162 bb = __floats2bfloat162_rn(__low2float(hh), __high2float(hh));
-              outw[2 * k + h] = *reinterpret_cast<const uint32_t*>(&bb);
+          for (int h = 0; h < 2; ++h) {
+            unsigned char* dst = h == 0 ? lo : hi;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {  // E4M3 chunk 4h + c -> BF16 chunks 2c, 2c + 1
+              const uint4 q = raw[4 * h + c];
+              const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+              uint32_t o[8];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                o[2 * k] = e4m3x2_to_bf16x2((uint16_t)(w[k] & 0xFFFFu));
+                o[2 * k + 1] = e4m3x2_to_bf16x2((uint16_t)(w[k] >> 16));
+              }
+              *reinterpret_cast<uint4*>(dst + ((((2 * c) ^ (y & 7)) & 7) << 4)) =
+                  make_uint4(o[0], o[1], o[2], o[3]);
+              *reinterpret_cast<uint4*>(dst + ((((2 * c + 1) ^ (y & 7)) & 7) << 4)) =
+                  make_uint4(o[4], o[5], o[6], o[7]);
             }
           }
-          // 16 features = two 16-byte chunks of BF16 region 2g + c8/4, chunks 2 (c8 % 4) + {0,1}
-          unsigned char* reg = dst + size_t(2 * g + (c8 >> 2)) * REG_BYTES + y * 128;
-          const int c16 = (c8 & 3) * 2;
-          *reinterpret_cast<uint4*>(reg + (((c16 ^ (y & 7)) & 7) << 4)) =
-              make_uint4(outw[0], outw[1], outw[2], outw[3]);
-          *reinterpret_cast<uint4*>(reg + ((((c16 + 1) ^ (y & 7)) & 7) << 4)) =
-              make_uint4(outw[4], outw[5], outw[6], outw[7]);
         }
         tc::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          tc::mbar_arrive(&full[b]);
-          tc::mbar_arrive(&qempty[qs]);
-        }
+        if (lane == 0) tc::mbar_arrive(&conv[st]);
       }
       if (!ok) fail();
     }
@@ -565,7 +571,7 @@ EncodeFn get_encode() {
 
 int rp_of(int r) { return r <= 8 ? 8 : 16; }
 
-TcExtra plan(int n, int r, bool fp8) {
+TcExtra plan(int n, int r, bool) {  // the same staging serves BF16 and E4M3 samples
   TcExtra ex{};
   ex.nload = (n + 63) / 64;
   ex.nreg = 2 * ((n + 127) / 128);
@@ -587,16 +593,6 @@ TcExtra plan(int n, int r, bool fp8) {
   ex.tmem_cols = pow2;
   ex.smem_bytes = fixed + S * stage;
   ex.nq = (n + 127) / 128;
-  ex.qstages = 0;
-  if (fp8) {
-    // two BF16 buffers for the MMAs, the rest of shared memory for the E4M3 ring
-    ex.stages = 2;
-    const int qstage = ex.nq * Q_BYTES;
-    int QS = (232448 - fixed - 2 * stage - 64 * 8) / qstage;
-    if (QS > 6) QS = 6;
-    ex.qstages = QS;
-    ex.smem_bytes = fixed + 2 * stage + QS * qstage + 64 * 8;
-  }
   return ex;
 }
 
@@ -621,7 +617,7 @@ size_t fg_tc_supported(int dtype, int n, int r) {
   if (r < 1 || r > 16 || n < 1 || n > 256) return 0;
   if (!get_encode()) return 0;
   const TcExtra ex = plan(n, r, dtype == STMF_E4M3);
-  return (dtype == STMF_E4M3 ? ex.qstages >= 2 : ex.stages >= 2) ? 1 : 0;
+  return ex.stages >= 2 ? 1 : 0;
 }
 
 int fg_tc_grid(int, int, int, int64_t p, int num_sms) {
