@@ -344,8 +344,7 @@ cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_f32_kernel<<<grid, NT, smem, s>>>(prm, sh);
-  return cudaGetLastError();
+  return launch_kernel(fg_f32_kernel, dim3(grid), dim3(NT), smem, s, prm, sh);
 }
 
 }  // namespace stmf

@@ -288,8 +288,7 @@ cudaError_t launch_one(const FgParams& prm, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_simt_kernel<TC, DT, JB, RRF, TS><<<grid, NT, smem, s>>>(prm);
-  return cudaGetLastError();
+  return launch_kernel(fg_simt_kernel<TC, DT, JB, RRF, TS>, dim3(grid), dim3(NT), smem, s, prm);
 }
 
 template <typename TC, int DT, bool RRF, int TS>

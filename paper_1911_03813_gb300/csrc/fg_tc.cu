@@ -606,8 +606,8 @@ cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtr
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  fg_tc_kernel<RP, FP8><<<grid, FP8 ? NTHREADS_FP8 : NTHREADS, ex.smem_bytes, s>>>(tmap, prm, ex);
-  return cudaGetLastError();
+  return launch_kernel(fg_tc_kernel<RP, FP8>, dim3(grid), dim3(FP8 ? NTHREADS_FP8 : NTHREADS),
+                       size_t(ex.smem_bytes), s, tmap, prm, ex);
 }
 
 }  // namespace

@@ -439,6 +439,7 @@ FitLayout layout(void* base, long long D, int m) {
 stmf_status FitRun::begin(stmf_ctx* c, const stmf_samples* V_, const double* nu_, int d_,
                           int64_t r_, const stmf_fit_opts* o, double* lambda, double* A,
                           cudaStream_t s) {
+  release();
   ctx = c;
   V = *V_;
   nu = nu_;
@@ -479,7 +480,55 @@ stmf_status FitRun::begin(stmf_ctx* c, const stmf_samples* V_, const double* nu_
   return STMF_OK;
 }
 
+GraphRecorder*& graph_recorder() {
+  static thread_local GraphRecorder* rec = nullptr;
+  return rec;
+}
+
+void FitRun::release() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  graph_ok = true;
+  chunks = 0;
+}
+
 stmf_status FitRun::enqueue_chunk(int32_t* done_host) {
+  // the first chunk runs as plain launches (kernel attributes get set up on first use); later
+  // ones replay a graph of the chunk, recorded once by the launchers themselves (no stream
+  // capture)
+  if (++chunks >= 2 && graph_ok) {
+    if (!graph) {
+      cudaGraph_t g = nullptr;
+      bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+      if (ok) {
+        GraphRecorder rec;
+        rec.graph = g;
+        graph_recorder() = &rec;
+        const stmf_status st = enqueue_body(done_host);
+        graph_recorder() = nullptr;
+        ok = st == STMF_OK && rec.ok && cudaGraphInstantiate(&graph, g, 0) == cudaSuccess;
+        cudaGraphDestroy(g);
+      }
+      if (!ok) {
+        graph = nullptr;
+        graph_ok = false;  // plain launches for the rest of this run
+        cudaGetLastError();
+      }
+    }
+    if (graph) {
+      if (cudaGraphLaunch(graph, stream) != cudaSuccess)
+        return set_error(ctx, STMF_ECUDA, "chunk graph launch");
+      enqueued += opts.chunk;
+      return STMF_OK;
+    }
+  }
+  const stmf_status st = enqueue_body(done_host);
+  if (st != STMF_OK) return st;
+  enqueued += opts.chunk;
+  return STMF_OK;
+}
+
+stmf_status FitRun::enqueue_body(int32_t* done_host) {
   FitLayout L = layout(ctx->fit_ws, D, opts.m);
   StepOpts so;
   so.pgtol = opts.pgtol;
@@ -494,19 +543,30 @@ stmf_status FitRun::enqueue_chunk(int32_t* done_host) {
     stmf_status st = enqueue_fg(ctx, &V, nu, d, r, L.xt, L.xt + r, &L.st->alpha, &L.st->ft,
                                 L.gt, L.gt + r, skip, stream);
     if (st != STMF_OK) return st;
-    lbfgs_step<<<1, LT, 0, stream>>>(L, so);
-    if (cudaGetLastError() != cudaSuccess) return set_error(ctx, STMF_ECUDA, "lbfgs_step launch");
+    if (launch_kernel(lbfgs_step, dim3(1), dim3(LT), 0, stream, L, so) != cudaSuccess)
+      return set_error(ctx, STMF_ECUDA, "lbfgs_step launch");
   }
-  enqueued += opts.chunk;
-  if (cudaMemcpyAsync(done_host, &L.st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) !=
-      cudaSuccess)
+  GraphRecorder* rec = graph_recorder();
+  if (rec) {
+    cudaGraphNode_t node;
+    if (cudaGraphAddMemcpyNode1D(&node, rec->graph, rec->last ? &rec->last : nullptr,
+                                 rec->last ? 1 : 0, done_host, &L.st->done, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rec->ok = false;
+      return set_error(ctx, STMF_ECUDA, "recording the done-flag copy");
+    }
+    rec->last = node;
+  } else if (cudaMemcpyAsync(done_host, &L.st->done, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             stream) != cudaSuccess) {
     return set_error(ctx, STMF_ECUDA, "reading the done flag");
+  }
   return STMF_OK;
 }
 
 bool FitRun::exhausted() const { return enqueued > opts.max_evals + opts.chunk; }
 
 stmf_status FitRun::finish(void* state_host) {
+  release();
   FitLayout L = layout(ctx->fit_ws, D, opts.m);
   fit_export<<<32, 256, 0, stream>>>(L, lam_out, A_out, (int)r, D);
   if (cudaGetLastError() != cudaSuccess) return set_error(ctx, STMF_ECUDA, "fit_export launch");

@@ -129,11 +129,9 @@ cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s) {
   const int nb = (L + RE - 1) / RE;
   if (prm.grid > RY * RMAX) return cudaErrorInvalidValue;
   const int nbB = (prm.r * prm.r + (RE * RY / 32) - 1) / (RE * RY / 32);
-  reduce_kernel<<<nb + nbB, RE * RY, 0, s>>>(prm, L, nb);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(reduce_kernel, dim3(nb + nbB), dim3(RE * RY), 0, s, prm, L, nb);
   if (e != cudaSuccess) return e;
-  finalize_kernel<<<(prm.n * prm.r + RT - 1) / RT, RT, 0, s>>>(prm);
-  return cudaGetLastError();
+  return launch_kernel(finalize_kernel, dim3((prm.n * prm.r + RT - 1) / RT), dim3(RT), 0, s, prm);
 }
 
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s) {

@@ -345,6 +345,7 @@ extern "C" stmf_status stmf_server_destroy(stmf_server_t srv) {
     if (r->fin) cudaEventDestroy(r->fin);
   }
   for (auto& s : srv->slots) {
+    s.run.release();
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.host_words) cudaFreeHost(s.host_words);

@@ -143,7 +143,7 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   prm.idx = idx;
   prm.rows = V_in->p;
   cudaEvent_t ev_end = nullptr;
-  if (c->profiling && c->ev_used + 2 <= 2 * 65536) {
+  if (c->profiling && !stmf::graph_recorder() && c->ev_used + 2 <= 2 * 65536) {
     while (c->ev_pool.size() < c->ev_used + 2) {
       cudaEvent_t ev;
       if (cudaEventCreate(&ev) != cudaSuccess) break;

@@ -195,14 +195,67 @@ struct FitRun {
   cudaStream_t stream = nullptr;
   long long D = 0;
   long long enqueued = 0;
+  // From the second chunk on, a chunk (its evaluations, steps and the done-flag copy) is replayed
+  // from a CUDA graph recorded once per run: the same launches with the same arguments every time.
+  cudaGraphExec_t graph = nullptr;
+  bool graph_ok = true;
+  int chunks = 0;
   stmf_status begin(stmf_ctx* c, const stmf_samples* V, const double* nu, int d, int64_t r,
                     const stmf_fit_opts* opts, double* lambda, double* A, cudaStream_t s);
   stmf_status enqueue_chunk(int32_t* done_host);
+  stmf_status enqueue_body(int32_t* done_host);
+  void release();  // destroys the chunk graph (begin and finish call it)
   bool exhausted() const;
   stmf_status finish(void* state_host);
   static size_t state_size();
   static void result_from(const void* state_host, int32_t dev_status, stmf_fit_result* out);
 };
+}  // namespace stmf
+
+namespace stmf {
+// Graph recording (the fit loop, lbfgs.cu): while a recorder is set for the calling thread, the
+// kernel launchers append kernel nodes, in order, to its graph instead of launching them. No
+// stream capture is involved, so other threads' device-wide synchronisation is unaffected.
+struct GraphRecorder {
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t last = nullptr;
+  bool ok = true;
+};
+GraphRecorder*& graph_recorder();
+
+template <typename T>
+struct NonDeduced {
+  using type = T;
+};
+
+#ifdef __CUDACC__
+// Launch kern<<<grid, block, smem, s>>>(args...), or record it when a recorder is active.
+template <typename... P>
+cudaError_t launch_kernel(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          typename NonDeduced<P>::type... args) {
+  GraphRecorder* rec = graph_recorder();
+  if (rec) {
+    void* ptrs[sizeof...(P) > 0 ? sizeof...(P) : 1] = {(void*)&args...};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)kern;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = ptrs;
+    cudaGraphNode_t node;
+    const cudaError_t e = cudaGraphAddKernelNode(&node, rec->graph, rec->last ? &rec->last : nullptr,
+                                                 rec->last ? 1 : 0, &kp);
+    if (e != cudaSuccess) {
+      rec->ok = false;
+      return e;
+    }
+    rec->last = node;
+    return cudaSuccess;
+  }
+  kern<<<grid, block, smem, s>>>(args...);
+  return cudaGetLastError();
+}
+#endif
 }  // namespace stmf
 
 // Record a device-side error in the status word: the first error wins.
