@@ -267,6 +267,16 @@ def alpha_bench(dev):
             "alpha": a.item()}
 
 
+METRIC = "f+grad evaluations/s (BF16 V; FP32 V beside it)"
+
+
+def workload_config(P, world):
+    return {"workload": WORKLOAD if P == P_FULL else "gmm_n256_d4_r16_p%d" % P,
+            "n": N_FEAT, "d": D, "r": R, "p": P, "sigma": SIGMA,
+            "l2": "inputs larger than L2 (8.6 GB BF16 per step)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -288,15 +298,15 @@ def run_reference(args):
     el = time.perf_counter() - t0
     per_full = el / steps * (P_FULL / p_sample)
     v = 1.0 / per_full
-    line = {"impl": "reference", "metric": "f+grad evaluations/s", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "evals/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
             "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "storage": "f64 (oracle)",
-                       "l2": "inputs larger than L2"},
+            "config": workload_config(P_FULL, 1),
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": len(os.sched_getaffinity(0)),
                              "kind": "oracle",
-                             "sample": "%d of %d samples per step, scaled by p" % (p_sample, P_FULL)},
+                             "sample": "FP64 oracle (NumPy) on %d of %d samples per step, "
+                                       "scaled by p" % (p_sample, P_FULL)},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -486,14 +496,11 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = ncu_traffic("fg_pass_bf16")
     line = {
-        "metric": "f+grad evaluations/s (BF16 V; FP32 V beside it)",
+        "metric": METRIC,
         "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms16 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD if P == P_FULL else "gmm_n256_d4_r16_p%d" % P,
-                   "n": N_FEAT, "d": D, "r": R, "p": P, "sigma": SIGMA,
-                   "l2": "inputs larger than L2 (8.6 GB BF16 per step)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(P, world),
         "hbm_gbs_over_V": bytes16 / (ms16 / args.steps / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": ach16, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": ach16 / peaks["hbm_gbs"], "traffic": traffic,
