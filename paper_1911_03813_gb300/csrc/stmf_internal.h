@@ -86,6 +86,7 @@ struct SymParams {
 size_t fg_simt_smem(int dtype, int n, int r);
 int fg_simt_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_simt_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+cudaError_t fg_simt_launch_f64(const FgParams& prm, int grid, cudaStream_t s);
 // Randomized range finder (eq. rrf): block partials of V Omega into prm.partials (w part zero).
 // f64: FP64 products and sums (needs fg_simt_smem(STMF_F64, n, r) <= 232448), else FP32 products
 // with FP32 sums folded into FP64 every prm.flush_tiles tiles.
