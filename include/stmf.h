@@ -193,7 +193,7 @@ STMF_API stmf_status stmf_fg_finish(stmf_ctx_t ctx, const double* yw, int64_t n,
  *  2  the distinct entries of the symmetric X (Sec. 3.3 notes that forming X can be cheaper than
  *     the implicit O(n p^2) route): X_m = sum_l nu_l prod_{i in m} v_li for every multiset m of
  *     d features and ||X||^2 = sum_m (d! / prod of the multiplicities' factorials) X_m^2, about
- *     p C(n+d-1, d) multiply-adds; needs C(n+d-2, d-1) <= 2^22 and, for FP64 samples, n <= 512
+ *     p C(n+d-1, d) multiply-adds; needs C(n+d-2, d-1) <= 2^22 and, for FP64 samples, n <= 384
  *     (the first call for an (n, d) builds a prefix table and synchronises the device);
  *  0  the cheaper of the two by their operation counts.
  * Per-block sums are combined in FP64 in a fixed order (reproducible bit for bit).

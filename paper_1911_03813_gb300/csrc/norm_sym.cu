@@ -64,20 +64,38 @@ __host__ __device__ inline int row_of(int n) {  // padded features per staged sa
   return (n + KT - 1) / KT * KT + 4;
 }
 
+// two sample-tile buffers (the next tile streams in while the current one is used, for FP32 and
+// FP64 samples), T, two buffers of nu, the block's prefixes
 template <typename TC>
 size_t smem_of(int n) {
-  return sizeof(TC) * (size_t(TSS) * row_of(n) + size_t(TSS) * PT + TSS) +
-         sizeof(uint16_t) * PT * 8;
+  return sizeof(TC) * (2 * size_t(TSS) * row_of(n) + size_t(TSS) * PT) +
+         sizeof(double) * 2 * TSS + sizeof(uint16_t) * PT * 8;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
 }
 
 template <typename TC, int DT>
 __global__ void __launch_bounds__(NT) norm_sym_kernel(const SymParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = prm.n, L = prm.d - 1, row = row_of(n);
-  TC* Vs = reinterpret_cast<TC*>(smem_raw);
-  TC* Ts = Vs + TSS * row;
-  TC* nus = Ts + TSS * PT;
-  uint16_t* Pidx = reinterpret_cast<uint16_t*>(nus + TSS);  // [PT][8]
+  TC* Vs0 = reinterpret_cast<TC*>(smem_raw);           // [2][TSS][row]
+  TC* Ts = Vs0 + 2 * TSS * row;                        // [TSS][PT]
+  double* nus0 = reinterpret_cast<double*>(Ts + TSS * PT);  // [2][TSS]
+  uint16_t* Pidx = reinterpret_cast<uint16_t*>(nus0 + 2 * TSS);  // [PT][8]
+  // samples already in the compute type stream in with cp.async, one tile ahead
+  constexpr bool kAsync = (DT == STMF_F32 && sizeof(TC) == 4) || (DT == STMF_F64 && sizeof(TC) == 8);
   const int tid = threadIdx.x;
   const int64_t p0 = int64_t(blockIdx.x) * PT;
   const int k0 = blockIdx.y * KT;
@@ -106,25 +124,66 @@ __global__ void __launch_bounds__(NT) norm_sym_kernel(const SymParams prm) {
     }
   const int64_t tiles = (prm.p + TSS - 1) / TSS;
   const int64_t t_lo = tiles * blockIdx.z / gridDim.z, t_hi = tiles * (blockIdx.z + 1) / gridDim.z;
+  // stage tile `tile` into buffer b: features past n and samples past p read as zero
+  auto stage = [&](int64_t tile, int b) {
+    TC* Vb = Vs0 + b * TSS * row;
+    double* nb = nus0 + b * TSS;
+    const int64_t s0 = tile * TSS;
+    if constexpr (kAsync) {
+      constexpr int EC = 16 / sizeof(TC);  // elements per 16-byte chunk
+      const int cpr = row / EC;
+      for (int e = tid; e < TSS * cpr; e += NT) {
+        const int s = e / cpr, c = e - s * cpr;
+        const int left = n - c * EC;
+        const uint32_t bytes =
+            (s0 + s < prm.p && left > 0) ? uint32_t((left >= EC ? EC : left) * sizeof(TC)) : 0u;
+        const TC* src = bytes ? reinterpret_cast<const TC*>(V) + (s0 + s) * prm.ld + c * EC
+                              : reinterpret_cast<const TC*>(V);
+        cp_async16(smem_u32(Vb + s * row + c * EC), src, bytes);
+      }
+      if (tid < TSS) {
+        const bool ok = s0 + tid < prm.p;
+        if (prm.nu)
+          cp_async8(smem_u32(nb + tid), ok ? prm.nu + s0 + tid : prm.nu, ok ? 8u : 0u);
+        else
+          nb[tid] = ok ? prm.nu_uniform : 0.0;
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    } else {
+      for (int e = tid; e < TSS * row; e += NT) {
+        const int s = e / row, i = e - s * row;
+        TC v = (TC)0;
+        if (i < n && s0 + s < prm.p) {
+          v = cv<TC>(V[(s0 + s) * prm.ld + i]);
+          if (DT == STMF_E4M3) v *= (TC)prm.scale[s0 + s];
+        }
+        Vb[e] = v;
+      }
+      if (tid < TSS)
+        nb[tid] = s0 + tid < prm.p ? (prm.nu ? prm.nu[s0 + tid] : prm.nu_uniform) : 0.0;
+    }
+  };
+  if (kAsync && t_lo < t_hi) stage(t_lo, 0);
   int since = 0;
   for (int64_t tile = t_lo; tile < t_hi; ++tile) {
-    const int64_t s0 = tile * TSS;
-    __syncthreads();  // the previous tile is done with Vs and Ts
-    for (int e = tid; e < TSS * row; e += NT) {
-      const int s = e / row, i = e - s * row;
-      TC v = (TC)0;
-      if (i < n && s0 + s < prm.p) {
-        v = cv<TC>(V[(s0 + s) * prm.ld + i]);
-        if (DT == STMF_E4M3) v *= (TC)prm.scale[s0 + s];
+    const int buf = kAsync ? int((tile - t_lo) & 1) : 0;
+    const TC* Vs = Vs0 + buf * TSS * row;
+    const double* nus = nus0 + buf * TSS;
+    __syncthreads();  // the previous tile is done with its buffer and with Ts
+    if constexpr (kAsync) {
+      if (tile + 1 < t_hi) {
+        stage(tile + 1, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
-      Vs[e] = v;
+    } else {
+      stage(tile, 0);
     }
-    if (tid < TSS)
-      nus[tid] = s0 + tid < prm.p ? (TC)(prm.nu ? prm.nu[s0 + tid] : prm.nu_uniform) : (TC)0;
     __syncthreads();
     for (int e = tid; e < TSS * PT; e += NT) {
       const int s = e / PT, q = e - s * PT;
-      TC t = nus[s];
+      TC t = (TC)nus[s];
       for (int j = 0; j < L; ++j) t *= Vs[s * row + Pidx[q * 8 + j]];
       Ts[e] = t;
     }
