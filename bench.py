@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--no-gram", action="store_true")
     ap.add_argument("--gmm-study", action="store_true",
                     help="run the Gaussian-mixture study grid of Sec. 4.2 (n=500) and print its line")
+    ap.add_argument("--alpha-only", action="store_true",
+                    help="only ||X||^2 from the distinct entries of X at n=100, p=2.5e6, d=3")
     ap.add_argument("--gram-only", action="store_true",
                     help="time only the ||X||^2 Gram pass on 2^16 samples and print it")
     ap.add_argument("--legs", default="bf16,fp32,fp8",
@@ -346,6 +348,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.gram_only:
         print(json.dumps(gram_bench(dev)), flush=True)
+        return
+    if args.alpha_only:
+        print(json.dumps(alpha_bench(dev)), flush=True)
         return
     if args.gmm_study:
         from paper_1911_03813_gb300 import study
