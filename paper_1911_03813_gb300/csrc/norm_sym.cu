@@ -8,7 +8,7 @@
 // Gram form, far less when p is large and n d small.
 //
 // A multiset is a sorted prefix P of d-1 features and a last feature k >= last(P). Block (x, y, z)
-// owns prefixes [64 x, 64 x + 64) of the lexicographically sorted prefix table, features
+// owns prefixes [64 x, 64 x + 64) of the prefix table (ordered by last feature), features
 // k in [64 y, 64 y + 64) and the z-th of S equal ranges of sample tiles: per 32-sample tile it
 // forms T[l][P] = nu_l prod_{i in P} v_li in shared memory, then X[P][k] += T[l][P] v_lk in 4 x 4
 // register blocks (FP32, folded into FP64 every 16 tiles; FP64 throughout for FP64 samples), and
@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "stmf_internal.h"
@@ -102,14 +103,18 @@ __global__ void __launch_bounds__(NT) norm_sym_kernel(const SymParams prm) {
   const int nk = int(gridDim.y) * KT;  // slab row length
   double* slab = prm.slabs + size_t(blockIdx.z) * size_t(prm.count) * nk;
 
+  __shared__ int min_last;
+  if (tid == 0) min_last = 1 << 30;
+  __syncthreads();
   for (int e = tid; e < PT * 8; e += NT) {
     const int q = e >> 3, j = e & 7;
     Pidx[e] = (p0 + q < prm.count && j < 7) ? prm.prefixes[p0 + q].idx[j] : 0;
+    if (j == L - 1 && p0 + q < prm.count) atomicMin(&min_last, int(Pidx[e]));
   }
   __syncthreads();
-  // every k of this block lies below the first feature of the block's first prefix, hence below
-  // last(P) for all its prefixes (sorted order): nothing to add
-  if (k0 + KT <= int(Pidx[0])) return;  // the squaring kernel skips these entries as well
+  // every k of this block lies below last(P) for all the block's prefixes: no valid entry (the
+  // squaring kernel reads only k >= last(P), so these slab entries are never needed)
+  if (k0 + KT <= min_last) return;
 
   const auto* V = reinterpret_cast<const typename St<DT>::T*>(prm.V);
   const int ty = tid >> 4, tx = tid & 15;  // prefixes 4 ty .. + 3, features k0 + 4 tx .. + 3
@@ -226,11 +231,7 @@ __global__ void __launch_bounds__(NT) sym_square_kernel(const SymParams prm, int
   if (q < prm.count) {
     const SymPrefix P = prm.prefixes[q];
     const int L = prm.d - 1, last = P.idx[L - 1];
-    // k-blocks below the first feature of the block's first prefix were never written
-    const int64_t qb = q / PT * PT;
-    const int kmin = int(prm.prefixes[qb].idx[0]) / KT * KT;
-    for (int k = last + lane; k < prm.n; k += 32) {
-      if (k < kmin) continue;
+    for (int k = last + lane; k < prm.n; k += 32) {  // every block holding such k wrote it
       double x = 0.0;
       for (int z = 0; z < S; ++z) x += prm.slabs[(size_t(z) * prm.count + q) * nk + k];
       const double m = k == last ? P.base / double(P.run + 1) : P.base;
@@ -302,6 +303,11 @@ void sym_prefixes(int n, int d, std::vector<SymPrefix>& out) {
     ++idx[j];
     for (int t = j + 1; t < L; ++t) idx[t] = idx[j];
   }
+  // order by last feature (stable): a block of 64 consecutive prefixes then has nearly equal
+  // last(P), and the blocks of features k below all of them have nothing to compute
+  std::stable_sort(out.begin(), out.end(), [L](const SymPrefix& a, const SymPrefix& b) {
+    return a.idx[L - 1] < b.idx[L - 1];
+  });
 }
 
 size_t norm_sym_smem(int dtype, int n) {

@@ -72,7 +72,7 @@ struct SymParams {
   const float* scale;
   const double* nu;
   double nu_uniform;
-  const SymPrefix* prefixes;  // [count], lexicographic
+  const SymPrefix* prefixes;  // [count], ordered by last feature
   long long count;
   double* slabs;     // [grid.z][count][grid.y * 64]: FP64 partial X per sample range
   double* partials;  // [blocks of the squaring kernel]
