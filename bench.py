@@ -267,6 +267,41 @@ def alpha_bench(dev):
             "alpha": a.item()}
 
 
+def fp32_scale_bench(dev, evals=1000):
+    """The FP32 workload at scale: n=100, p=2.5e6 (10 means, sigma=0.1, Dirichlet weights),
+    r=10, a timed batch of `evals` evaluations, each at its own random (lambda, A), for d=3 and
+    d=4 (CUDA events; the 1 GB of FP32 samples is larger than L2)."""
+    import numpy as np
+    import torch
+
+    from paper_1911_03813_gb300 import inputs, stmf
+    n, p, r = 100, 2500000, 10
+    st = inputs.gmm_device(n, p, 10, 0.1, SEED + 11, dev, out_dtype="f32")
+    models = [inputs.random_model(n, r, seed=SEED + 100 + k) for k in range(evals)]
+    lams = torch.tensor(np.stack([m[0] for m in models]), device=dev)
+    As = torch.tensor(np.stack([np.ascontiguousarray(m[1].T) for m in models]), device=dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    gl = torch.empty(r, dtype=torch.float64, device=dev)
+    GA = torch.empty((r, n), dtype=torch.float64, device=dev).T
+    stmf.reserve(st, r)
+    out = {}
+    for d in (3, 4):
+        for k in range(3):
+            stmf.fg(st, None, d, lams[k], As[k].T, out=(f, gl, GA))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(evals):
+            stmf.fg(st, None, d, lams[k], As[k].T, out=(f, gl, GA))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / evals
+        out["d%d" % d] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms,
+                          "gbs_over_V": p * n * 4 / (ms / 1e3) / 1e9}
+    del st
+    return {"n": n, "p": p, "r": r, "dtype": "f32", "evals": evals, **out}
+
+
 METRIC = "f+grad evaluations/s (BF16 V; FP32 V beside it)"
 
 
@@ -497,6 +532,7 @@ def main():
     torch.cuda.empty_cache()
     gram = None if args.no_gram else gram_bench(dev)
     alpha = None if args.no_gram else alpha_bench(dev)
+    fp32_scale = None if args.no_gram else fp32_scale_bench(dev)
     serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = ncu_traffic("fg_pass_bf16")
@@ -525,6 +561,7 @@ def main():
         "e2e": e2e,
         "gram": gram,
         "alpha_fp32_scale": alpha,
+        "fp32_scale": fp32_scale,
         "serving": serving,
         "cpu_baseline": cpu,
     }
