@@ -1,6 +1,6 @@
 // Fused pass over FP32 samples on the CUDA cores, register-blocked (r <= 16, n <= 256).
 //
-// Per persistent block and over that block's tiles of TS = 64 samples it accumulates the partial
+// Per persistent block and over that block's tiles of TS samples it accumulates the partial
 // sums of Alg. 2 line 2 (Lemma 3.3, eq. Y) and Lemma 3.5:
 //     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
 // reading every sample from HBM once. The arithmetic is 2 n r FMA per sample per product (Z = V A
@@ -10,15 +10,19 @@
 // broadcast), and the next tile streams into the other shared-memory buffer with cp.async while
 // the current one is used.
 //
-// Per tile (256 threads, 8 warps):
-//   phase 1  Z = V_t A          warp w: samples [32 (w & 1), +32), features of quarter w >> 1;
+// Per tile (NW warps; SH = TS / 32 sample halves, KS = NW / SH feature splits):
+//   phase 1  Z = V_t A          warp w: samples [32 (w % SH), +32), features of split w / SH;
 //                               lane: samples g, g+8, g+16, g+24 (g = lane / 4) x columns
-//                               4 (lane % 4) .. +3; the four quarter partials go to shared memory
-//   weights  z = sum of the 4 quarter partials (fixed order); W = nu z^{d-1}; w += nu z^d
+//                               4 (lane % 4) .. +3; the KS split partials go to shared memory
+//   weights  z = sum of the KS split partials (fixed order); W = nu z^{d-1}; w += nu z^d
 //   phase 2  Y += V_t^T W       warp: 32 features (lane: 4 features x 4 columns) over its share
-//                               of the tile's samples (warps split the samples when n < 256)
+//                               of the tile's samples (warps split the samples when n is small)
+// Each phase ends at a block barrier. The pass runs 32-sample tiles with 8 warps and two blocks
+// per SM, so that one block's barrier waits overlap the other block's arithmetic (measured
+// against 64-sample tiles with 16 warps and one block per SM: 8.6 against 9.4 ms at n = 256,
+// r = 16, p = 2^24, and 0.80 against 1.13 ms at n = 100, r = 10, p = 2.5e6).
 // Y is folded from FP32 into the block's FP64 partial and w into FP64 registers every
-// `flush_tiles` tiles, in a fixed order (results reproducible bit for bit).
+// 64 flush_tiles samples, in a fixed order (results reproducible bit for bit).
 #include <cuda_runtime.h>
 
 #include "stmf_internal.h"
@@ -26,13 +30,23 @@
 namespace stmf {
 namespace {
 
-constexpr int TS = 64;   // samples per tile
-constexpr int NW = 16;   // warps per block
-constexpr int NT = 32 * NW;
-constexpr int RC = 16;   // columns of A handled (r <= 16, zero-padded)
-constexpr int KS = NW / 2;        // phase 1: K splits (x 2 sample halves of 32)
-constexpr int EPT = TS * RC / NT;  // weights: (sample, column) entries per thread
-constexpr int CPT = RC / EPT;      // weights: threads per sample
+constexpr int RC = 16;  // columns of A handled (r <= 16, zero-padded)
+constexpr int KS = 8;   // phase 1: K splits (NW / (TS / 32))
+
+// TS samples per tile, NW warps per block, MB blocks per SM
+template <int TS_, int NW_, int MB_>
+struct Cfg {
+  static constexpr int TS = TS_;
+  static constexpr int NW = NW_;
+  static constexpr int MB = MB_;
+  static constexpr int NT = 32 * NW;
+  static constexpr int SH = TS / 32;         // phase 1: sample halves of 32
+  static constexpr int EPT = TS * RC / NT;   // weights: (sample, column) entries per thread
+  static constexpr int CPT = RC / EPT;       // weights: threads per sample
+  static_assert(NW / SH == KS, "phase 1 splits the features KS ways");
+  static_assert(NT == TS * CPT, "one weights thread per (sample, column group)");
+};
+using CfgPair = Cfg<32, 8, 2>;
 
 struct Shape {
   int np;      // features padded to a multiple of 4 KS (each K split a multiple of 4)
@@ -42,6 +56,7 @@ struct Shape {
   int ss;      // sample splits in phase 2 (NW / p2)
 };
 
+template <class C>
 Shape shape_of(int n) {
   Shape s;
   s.np = (n + 4 * KS - 1) / (4 * KS) * (4 * KS);
@@ -50,11 +65,13 @@ Shape shape_of(int n) {
   const int nfb = (s.np + 31) / 32;
   s.p2 = 1;
   while (s.p2 < nfb) s.p2 <<= 1;
-  s.ss = NW / s.p2;
+  s.ss = C::NW / s.p2;
   return s;
 }
 
+template <class C>
 size_t smem_of(const Shape& s) {
+  constexpr int TS = C::TS;
   return sizeof(float) * (2 * size_t(TS) * s.pitch  // V tiles (double buffer)
                           + size_t(s.np) * RC       // A
                           + KS * TS * RC            // K-split partials of Z (reused at the end)
@@ -99,8 +116,10 @@ struct StageWalk {
   int s, c, ds, dc, cpr;
 };
 
+template <class C>
 __device__ __forceinline__ void stage_tile(const FgParams& prm, const Shape& sh, const StageWalk& w,
                                            float* Vbuf, double* nubuf, int64_t tile) {
+  constexpr int TS = C::TS;
   const float* V = static_cast<const float*>(prm.V);
   const int64_t s0 = tile * TS;
   int s = w.s, c = w.c;
@@ -135,7 +154,9 @@ __device__ __forceinline__ void stage_tile(const FgParams& prm, const Shape& sh,
   }
 }
 
-__global__ void __launch_bounds__(NT, 1) fg_f32_kernel(const FgParams prm, const Shape sh) {
+template <class C>
+__global__ void __launch_bounds__(C::NT, C::MB) fg_f32_kernel(const FgParams prm, const Shape sh) {
+  constexpr int TS = C::TS, NT = C::NT, SH = C::SH, EPT = C::EPT, CPT = C::CPT;
   if (prm.skip && *prm.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Vs = reinterpret_cast<float*>(smem_raw);
@@ -163,7 +184,7 @@ __global__ void __launch_bounds__(NT, 1) fg_f32_kernel(const FgParams prm, const
   walk.dc = NT - walk.ds * walk.cpr;
 
   // phase 1 roles
-  const int h1 = warp & 1, q1 = warp >> 1;
+  const int h1 = warp % SH, q1 = warp / SH;
   const int g1 = lane >> 2, cg = lane & 3;
   // weights role: sample sw, columns EPT cw .. EPT cw + EPT - 1
   const int sw = tid / CPT, cw = tid % CPT;
@@ -186,14 +207,15 @@ __global__ void __launch_bounds__(NT, 1) fg_f32_kernel(const FgParams prm, const
   for (int a = 0; a < 4; ++a) yacc[a][0] = yacc[a][1] = make_float2(0.f, 0.f);
   bool first_flush = true;
 
-  if (my_tiles > 0) stage_tile(prm, sh, walk, Vs, nus, blockIdx.x);
+  const int flush_every = prm.flush_tiles * (64 / TS);
+  if (my_tiles > 0) stage_tile<C>(prm, sh, walk, Vs, nus, blockIdx.x);
   cp_async_commit();
   int since_flush = 0;
   for (int it = 0; it < my_tiles; ++it) {
     const int buf = it & 1;
     const float* Vt = Vs + buf * TS * sh.pitch;
     if (it + 1 < my_tiles)
-      stage_tile(prm, sh, walk, Vs + (buf ^ 1) * TS * sh.pitch, nus + (buf ^ 1) * TS,
+      stage_tile<C>(prm, sh, walk, Vs + (buf ^ 1) * TS * sh.pitch, nus + (buf ^ 1) * TS,
                  blockIdx.x + int64_t(it + 1) * gridDim.x);
     cp_async_commit();
     cp_async_wait<1>();  // this tile's copies (the older group) have landed
@@ -272,7 +294,7 @@ __global__ void __launch_bounds__(NT, 1) fg_f32_kernel(const FgParams prm, const
         }
       }
     }
-    if (++since_flush == prm.flush_tiles || it == my_tiles - 1) {
+    if (++since_flush == flush_every || it == my_tiles - 1) {
       since_flush = 0;
 #pragma unroll
       for (int a = 0; a < EPT; ++a) {
@@ -326,25 +348,38 @@ bool fg_f32_supported(int dtype, int n, int r) {
   return dtype == STMF_F32 && n >= 1 && n <= 256 && r >= 1 && r <= RC;
 }
 
-int fg_f32_grid(int, int64_t p, int num_sms) {
-  // one block per SM (shared memory and registers)
-  const int64_t tiles = (p + TS - 1) / TS;
-  int64_t grid = num_sms;
+namespace {
+
+template <class C>
+int grid_of(int64_t p, int num_sms) {
+  // C::MB persistent blocks per SM (shared memory and registers)
+  const int64_t tiles = (p + C::TS - 1) / C::TS;
+  int64_t grid = int64_t(num_sms) * C::MB;
   if (grid > tiles) grid = tiles;
   return (int)(grid < 1 ? 1 : grid);
 }
 
-cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s) {
-  const Shape sh = shape_of(prm.n);
-  const size_t smem = smem_of(sh);
+template <class C>
+cudaError_t launch_cfg(const FgParams& prm, int grid, cudaStream_t s) {
+  const Shape sh = shape_of<C>(prm.n);
+  const size_t smem = smem_of<C>(sh);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         232448);
+    cudaError_t e = cudaFuncSetAttribute(fg_f32_kernel<C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem_of<C>(shape_of<C>(256))));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  return launch_kernel(fg_f32_kernel, dim3(grid), dim3(NT), smem, s, prm, sh);
+  return launch_kernel(fg_f32_kernel<C>, dim3(grid), dim3(C::NT), smem, s, prm, sh);
+}
+
+}  // namespace
+
+int fg_f32_grid(int, int64_t p, int num_sms) { return grid_of<CfgPair>(p, num_sms); }
+
+cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_cfg<CfgPair>(prm, grid, s);
 }
 
 }  // namespace stmf
