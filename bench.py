@@ -302,6 +302,40 @@ def fp32_scale_bench(dev, evals=1000):
     return {"n": n, "p": p, "r": r, "dtype": "f32", "evals": evals, **out}
 
 
+def autograd_bench(dev, calls=50):
+    """The differentiation workload: n=64, d=3, r=8, p=1e6 FP32 samples; the autograd.Function
+    over (lambda, A) timed per call, forward (the fused pass and the model terms) against
+    backward (the stored gradient scaled by the incoming gradient), CUDA events."""
+    import torch
+
+    from paper_1911_03813_gb300 import autograd, inputs
+    n, p, r, d = 64, 1000000, 8, 3
+    st = inputs.gmm_device(n, p, r, 0.1, SEED + 21, dev, out_dtype="f32")
+    lam0, A0 = inputs.random_model(n, r, seed=SEED + 22)
+    lam = torch.tensor(lam0, device=dev, requires_grad=True)
+    A = torch.tensor(A0, device=dev, requires_grad=True)
+    for _ in range(3):
+        autograd.objective(lam, A, st, None, d).backward()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for _ in range(calls):
+        lam.grad = None
+        A.grad = None
+        torch.cuda.synchronize()
+        ev[0].record()
+        f = autograd.objective(lam, A, st, None, d)
+        ev[1].record()
+        f.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        fwd += ev[0].elapsed_time(ev[1])
+        bwd += ev[1].elapsed_time(ev[2])
+    del st
+    return {"n": n, "p": p, "r": r, "d": d, "dtype": "f32", "calls": calls,
+            "forward_ms": fwd / calls, "backward_ms": bwd / calls,
+            "backward_over_forward": bwd / fwd}
+
+
 METRIC = "f+grad evaluations/s (BF16 V; FP32 V beside it)"
 
 
@@ -533,6 +567,7 @@ def main():
     gram = None if args.no_gram else gram_bench(dev)
     alpha = None if args.no_gram else alpha_bench(dev)
     fp32_scale = None if args.no_gram else fp32_scale_bench(dev)
+    differentiation = None if args.no_gram else autograd_bench(dev)
     serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     traffic = ncu_traffic("fg_pass_bf16")
@@ -562,6 +597,7 @@ def main():
         "gram": gram,
         "alpha_fp32_scale": alpha,
         "fp32_scale": fp32_scale,
+        "differentiation": differentiation,
         "serving": serving,
         "cpu_baseline": cpu,
     }
