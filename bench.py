@@ -30,8 +30,8 @@ def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         pk = json.load(open(path))
-        return dict(hbm_gbs=pk["hbm_gbs"], src="measured")
-    return dict(hbm_gbs=6800.0, src="fallback")
+        return dict(hbm_gbs=pk["hbm_gbs"], sm_max_mhz=pk.get("sm_max_mhz", 2070.0), src="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
 
 
 class ClockSampler:
@@ -513,6 +513,10 @@ def main():
     peaks = measured_peaks()
     ach16 = bytes16 / (pass16 / 1e3) / 1e9
     ach32 = bytes32 / (pass32 / 1e3) / 1e9
+    # the FP32 pass is bound by the FP32 pipe: Z = V^T A and Y += V W are 2 n r FMA per sample
+    flop32 = 4 * P * N_FEAT * R
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
 
     # end to end through the public API with host buffers: stmf_fg_host streams V from pinned
     # host memory in chunks (copies overlapped with the passes) and returns f and g to the host
@@ -585,6 +589,12 @@ def main():
         "fp32": {"value": steps32 / (ms32 / 1e3) * world, "unit": "evals/s",
                  "ms_per_step": ms32 / steps32, "hbm_gbs_over_V": bytes32 / (ms32 / steps32 / 1e3) / 1e9,
                  "pass_frac_of_hbm": ach32 / peaks["hbm_gbs"],
+                 "roofline": {"bound": "alu", "achieved": flop32 / (pass32 / 1e3) / 1e12,
+                              "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": flop32 / (pass32 / 1e3) / 1e12 / fp32_peak,
+                              "traffic": None, "kernel": "fused pass, FP32 samples (CUDA cores)",
+                              "peak_src": "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                              "algorithmic_flop_per_launch": flop32},
                  "bf16_over_fp32": (args.steps / ms16) / (steps32 / ms32)},
         "fp8": {"value": args.steps / (ms8 / 1e3) * world, "unit": "evals/s",
                 "ms_per_step": ms8 / args.steps,
