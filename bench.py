@@ -113,17 +113,45 @@ def ncu_traffic(kernel_tag):
     return t.get("dram_bytes_per_launch_full")
 
 
-def cpu_baseline(seconds=12.0, p_sample=1 << 17):
+def cpu_baseline(dev, seconds=12.0, p_sample=1 << 17):
     """The FP64 oracle (NumPy, host BLAS threads) on a bounded sample of the workload, scaled to
-    full-workload evaluations per second."""
+    full-workload evaluations per second. Beside it, the GPU's f, g_lambda and G_A on the same
+    sample in each storage type against the oracle: on the stored (rounded) values, which is
+    the error of the GPU arithmetic, and on the FP64 samples, which adds the rounding of V."""
     import numpy as np
+    import torch
 
     import oracle
-    from paper_1911_03813_gb300 import inputs
+    from oracle import formats
+    from paper_1911_03813_gb300 import inputs, stmf
     data = inputs.gmm(N_FEAT, p_sample, N_MEANS, SIGMA, seed=SEED)
     Vt = np.ascontiguousarray(data["V"].T)
     lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
-    oracle.fg_implicit(None, Vt, lam, A, D)
+    ref64 = oracle.fg_implicit(None, Vt, lam, A, D)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+    accuracy = {}
+    lam_t = torch.tensor(lam, device=dev)
+    A_t = torch.tensor(np.ascontiguousarray(A.T), device=dev).T
+    for dt in ("bf16", "f32", "e4m3"):
+        st = inputs.to_storage(data["V"], dt, device=dev)
+        f, gl, GA = stmf.fg(st, None, D, lam_t, A_t)
+        got = (f.item(), gl.cpu().numpy(), GA.cpu().numpy())
+        bits = inputs.storage_bits(st)
+        stored = (formats.decode_bf16(bits) if dt == "bf16" else
+                  formats.dequantize_e4m3(bits, st["scale"].cpu().numpy()) if dt == "e4m3" else
+                  np.asarray(bits, dtype=np.float64))
+        ref = oracle.fg_implicit(None, np.ascontiguousarray(stored.T), lam, A, D)
+        accuracy[dt] = {
+            "vs_oracle_on_stored_values": {"f": abs(got[0] - ref[0]) / abs(ref[0]),
+                                           "g_lambda": rel(got[1], ref[1]),
+                                           "G_A": rel(got[2], ref[2])},
+            "vs_oracle_on_fp64_samples": {"f": abs(got[0] - ref64[0]) / abs(ref64[0]),
+                                          "g_lambda": rel(got[1], ref64[1]),
+                                          "G_A": rel(got[2], ref64[2])}}
+        del st
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -137,7 +165,8 @@ def cpu_baseline(seconds=12.0, p_sample=1 << 17):
     cores = len(os.sched_getaffinity(0))
     return dict(value=1.0 / per_eval_full, unit="evals/s", cores=cores, kind="oracle",
                 sample="%d of %d samples (n=%d, d=%d, r=%d), %d evaluations in %.1f s, scaled "
-                       "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el))
+                       "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el),
+                accuracy=accuracy)
 
 
 def make_requests(count, seed, dev):
@@ -573,7 +602,7 @@ def main():
     fp32_scale = None if args.no_gram else fp32_scale_bench(dev)
     differentiation = None if args.no_gram else autograd_bench(dev)
     serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
-    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    cpu = None if args.no_cpu_baseline else cpu_baseline(dev)
     traffic = ncu_traffic("fg_pass_bf16")
     line = {
         "metric": METRIC,
