@@ -28,6 +28,9 @@
  *    stmf_device_status().
  *  - Asynchrony: stmf_fg and stmf_norm_x only enqueue work on `stream` (NULL = the legacy
  *    default stream) and return; their outputs are valid once the stream reaches that point.
+ *  - Devices: a context is bound to the device it was created on. Make that device current
+ *    (cudaSetDevice) on the calling thread before each call, as for a cuBLAS handle; a call
+ *    made with another device current returns STMF_EINVAL before anything is launched.
  *  - Threads and streams: a context may be used from one host thread at a time, and calls on
  *    different streams that share a context must not overlap on the device (they share the
  *    context's workspace). Use one context per concurrent stream.

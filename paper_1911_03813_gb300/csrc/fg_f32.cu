@@ -363,14 +363,8 @@ template <class C>
 cudaError_t launch_cfg(const FgParams& prm, int grid, cudaStream_t s) {
   const Shape sh = shape_of<C>(prm.n);
   const size_t smem = smem_of<C>(sh);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_f32_kernel<C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem_of<C>(shape_of<C>(256))));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = smem_limit((const void*)fg_f32_kernel<C>, int(smem_of<C>(shape_of<C>(256))));
+  if (e != cudaSuccess) return e;
   return launch_kernel(fg_f32_kernel<C>, dim3(grid), dim3(C::NT), smem, s, prm, sh);
 }
 

@@ -288,13 +288,8 @@ int tile_of(int n, int rp) {
 template <typename TC, int DT, int JB, bool RRF, int TS>
 cudaError_t launch_one(const FgParams& prm, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes<TC>(prm.n, prm.r_pad, TS);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_simt_kernel<TC, DT, JB, RRF, TS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = smem_limit((const void*)fg_simt_kernel<TC, DT, JB, RRF, TS>, kSmemMax);
+  if (e != cudaSuccess) return e;
   return launch_kernel(fg_simt_kernel<TC, DT, JB, RRF, TS>, dim3(grid), dim3(NT), smem, s, prm);
 }
 

@@ -599,13 +599,8 @@ TcExtra plan(int n, int r, bool) {  // the same staging serves BF16 and E4M3 sam
 template <int RP, bool FP8>
 cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtra& ex, int grid,
                       cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fg_tc_kernel<RP, FP8>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = smem_limit((const void*)fg_tc_kernel<RP, FP8>, 232448);
+  if (e != cudaSuccess) return e;
   return launch_kernel(fg_tc_kernel<RP, FP8>, dim3(grid), dim3(FP8 ? NTHREADS_FP8 : NTHREADS),
                        size_t(ex.smem_bytes), s, tmap, prm, ex);
 }

@@ -143,13 +143,8 @@ size_t gram_smem(int n) {
 
 template <typename TC, int DT>
 cudaError_t launch(const GramParams& prm, int grid, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(gram_simt_kernel<TC, DT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = smem_limit((const void*)gram_simt_kernel<TC, DT>, 232448 - 1024);
+  if (e != cudaSuccess) return e;
   gram_simt_kernel<TC, DT><<<grid, NT, gram_smem<TC>(prm.n), s>>>(prm);
   return cudaGetLastError();
 }

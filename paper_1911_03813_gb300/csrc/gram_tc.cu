@@ -296,13 +296,8 @@ EncodeFn encoder() {
 
 template <int DP>
 cudaError_t launch_d(const CUtensorMap& tmap, const GramTcParams& prm, int grid, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<DP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const cudaError_t e = smem_limit((const void*)gram_tc_kernel<DP>, 232448);
+  if (e != cudaSuccess) return e;
   gram_tc_kernel<DP><<<grid, NTHREADS, prm.smem_bytes, s>>>(tmap, prm);
   return cudaGetLastError();
 }

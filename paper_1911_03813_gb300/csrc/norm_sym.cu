@@ -252,15 +252,9 @@ __global__ void __launch_bounds__(NT) sym_square_kernel(const SymParams prm, int
 
 template <typename TC, int DT>
 cudaError_t launch(const SymParams& prm, dim3 grid, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    // the opt-in limit covers static shared memory too (the kernel's reduction array)
-    cudaError_t e = cudaFuncSetAttribute(norm_sym_kernel<TC, DT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         232448 - 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // the opt-in limit covers static shared memory too (the kernel's reduction array)
+  const cudaError_t e = smem_limit((const void*)norm_sym_kernel<TC, DT>, 232448 - 1024);
+  if (e != cudaSuccess) return e;
   norm_sym_kernel<TC, DT><<<grid, NT, smem_of<TC>(prm.n), s>>>(prm);
   return cudaGetLastError();
 }

@@ -4,7 +4,9 @@
 #include <stdio.h>
 
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -24,6 +26,14 @@ stmf_status cuda_fail(stmf_ctx* c, cudaError_t e, const char* where) {
   return fail(c, STMF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// A context's arrays and workspace live on its device: every call runs with that device current.
+stmf_status check_device(stmf_ctx* c) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device)
+    return fail(c, STMF_EINVAL, "the context's device is not the calling thread's current device");
+  return STMF_OK;
+}
+
 stmf_status check_samples(stmf_ctx* c, const stmf_samples* V) {
   if (!V) return fail(c, STMF_EINVAL, "V is NULL");
   if (!V->data) return fail(c, STMF_EINVAL, "V->data is NULL");
@@ -37,7 +47,7 @@ stmf_status check_samples(stmf_ctx* c, const stmf_samples* V) {
   if ((reinterpret_cast<uintptr_t>(V->data) & 15) != 0) return fail(c, STMF_EINVAL, "V->data must be 16-byte aligned");
   if (V->dtype == STMF_E4M3 && !V->scale) return fail(c, STMF_EINVAL, "E4M3 samples need V->scale");
   if (V->dtype != STMF_E4M3 && V->scale) return fail(c, STMF_EINVAL, "V->scale is only used with E4M3 samples");
-  return STMF_OK;
+  return check_device(c);
 }
 
 stmf_status ensure_ws(stmf_ctx* c, size_t bytes) {
@@ -82,6 +92,21 @@ size_t fg_ws_bytes(const FgPlan& pl, int64_t r) {
 size_t gram_ws_bytes(int grid) { return size_t(grid) * sizeof(double); }
 
 }  // namespace
+
+cudaError_t stmf::smem_limit(const void* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> limit set
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  const auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
+}
 
 stmf_status stmf::set_error(stmf_ctx* c, stmf_status st, const std::string& msg) {
   return fail(c, st, msg);
@@ -260,6 +285,7 @@ const char* stmf_last_error(stmf_ctx_t c) { return c ? c->last_error.c_str() : "
 
 stmf_status stmf_device_status(stmf_ctx_t c, stmf_stream_t stream, int32_t* out_host) {
   if (!c || !out_host) return fail(c, STMF_EINVAL, "NULL argument");
+  if (check_device(c) != STMF_OK) return STMF_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, c->status, sizeof(v), cudaMemcpyDeviceToHost, s);
@@ -371,7 +397,9 @@ stmf_status stmf_fg_finish(stmf_ctx_t c, const double* yw, int64_t n, int32_t d,
     return fail(c, STMF_EINVAL, "NULL argument");
   if (n < 1 || n > kMaxN || r < 1 || r > 64 || d < 2 || d > 8)
     return fail(c, STMF_EINVAL, "n, r or d out of range");
-  stmf_status st = ensure_ws(c, size_t(r) * size_t(r) * sizeof(double));
+  stmf_status st = check_device(c);
+  if (st != STMF_OK) return st;
+  st = ensure_ws(c, size_t(r) * size_t(r) * sizeof(double));
   if (st != STMF_OK) return st;
   stmf::ModelParams mp{};
   mp.A = A;
@@ -403,6 +431,7 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   if ((V->dtype == STMF_E4M3) != (V->scale != nullptr))
     return fail(c, STMF_EINVAL, "E4M3 samples need scales (and only they)");
   if (d < 2 || d > 8 || r < 1 || r > 64) return fail(c, STMF_EINVAL, "d or r out of range");
+  if (check_device(c) != STMF_OK) return STMF_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = V->n, p = V->p;
   const size_t row_bytes = size_t(V->ld) * eb;

@@ -224,6 +224,10 @@ struct GraphRecorder {
 };
 GraphRecorder*& graph_recorder();
 
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current device, once per
+// (kernel, device); safe to call from several host threads.
+cudaError_t smem_limit(const void* kernel, int bytes);
+
 template <typename T>
 struct NonDeduced {
   using type = T;
