@@ -343,7 +343,9 @@ STMF_API stmf_status stmf_submit(stmf_server_t srv, const stmf_request* req, uin
 
 /* Wait up to timeout_ms (0: do not wait, < 0: no limit) for the request; fills *out (host) and
  * returns STMF_OK once it has finished (successfully or not: see out->state), STMF_ENOTREADY
- * while it is queued or running, STMF_EINVAL for an unknown ticket. */
+ * while it is queued or running, STMF_EINVAL for an unknown ticket. The call that returns
+ * STMF_OK delivers the result once and releases the ticket: later polls or cancels of it
+ * return STMF_EINVAL, so a long-running server holds no memory for delivered requests. */
 STMF_API stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_request_result* out,
                       int32_t timeout_ms);
 

@@ -376,9 +376,20 @@ extern "C" stmf_status stmf_submit(stmf_server_t srv, const stmf_request* q, uin
   r->footprint =
       ((r->v_bytes + r->s_bytes + 255) & ~size_t(255)) + sizeof(double) * r->x0.size() + 256;
   if (r->footprint > srv->avail) return STMF_ENOMEM;
-  if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->fin, cudaEventDisableTiming) != cudaSuccess)
-    return STMF_ECUDA;
+  {
+    // the request's events belong to the server's device, whatever device the caller has current
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return STMF_ECUDA;
+    if (prev != srv->cfg.device && cudaSetDevice(srv->cfg.device) != cudaSuccess)
+      return STMF_ECUDA;
+    const bool ok = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&r->fin, cudaEventDisableTiming) == cudaSuccess;
+    if (prev != srv->cfg.device) cudaSetDevice(prev);
+    if (!ok) {
+      if (r->ready) cudaEventDestroy(r->ready);
+      return STMF_ECUDA;
+    }
+  }
   std::lock_guard<std::mutex> lock(srv->mu);
   r->ticket = srv->next_ticket++;
   r->t_submit = srv->now();
@@ -393,19 +404,27 @@ extern "C" stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_reques
                                  int32_t timeout_ms) {
   if (!srv || !out) return STMF_EINVAL;
   std::unique_lock<std::mutex> lock(srv->mu);
-  auto it = srv->all.find(ticket);
-  if (it == srv->all.end()) return STMF_EINVAL;
-  Request* r = it->second.get();
-  auto done = [r]() { return r->state == RQ_DONE; };
-  if (!done()) {
-    if (timeout_ms < 0) srv->cv.wait(lock, done);
-    else if (timeout_ms > 0) srv->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), done);
+  // the request is looked up again after every wait: a concurrent poll may release it
+  auto find = [srv, ticket]() -> Request* {
+    auto it = srv->all.find(ticket);
+    return it == srv->all.end() ? nullptr : it->second.get();
+  };
+  auto settled = [&find]() {
+    Request* q = find();
+    return !q || q->state == RQ_DONE;
+  };
+  if (!find()) return STMF_EINVAL;
+  if (!settled()) {
+    if (timeout_ms < 0) srv->cv.wait(lock, settled);
+    else if (timeout_ms > 0) srv->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), settled);
   }
+  Request* r = find();
+  if (!r) return STMF_EINVAL;
   std::memset(out, 0, sizeof(*out));
   out->t_submit = r->t_submit;
   out->t_admit = r->t_admit;
   out->footprint = r->footprint;
-  if (!done()) {
+  if (r->state != RQ_DONE) {
     out->state = STMF_ENOTREADY;
     return STMF_ENOTREADY;
   }
@@ -414,6 +433,11 @@ extern "C" stmf_status stmf_poll(stmf_server_t srv, uint64_t ticket, stmf_reques
   out->best = r->best;
   out->total_evals = r->total_evals;
   out->t_done = r->t_done;
+  // the result has been delivered: release the ticket (no queue, slot or stream refers to a
+  // finished request, and its device memory went back at finalisation)
+  if (r->ready) cudaEventDestroy(r->ready);
+  if (r->fin) cudaEventDestroy(r->fin);
+  srv->all.erase(ticket);
   return STMF_OK;
 }
 

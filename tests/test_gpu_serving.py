@@ -147,3 +147,5 @@ def test_cancel_invalid_and_nonfinite(stmf):
         assert res["state"] == 0 and res["stop"] == 6   # finished: non-finite objective
         t3 = srv.submit(V, d, x0, pgtol=1e-6, max_evals=200, alpha_mode=0)
         assert srv.poll(t3)["state"] == 0               # the server keeps serving
+        with pytest.raises(stmf.StmfError):
+            srv.poll(t3)                                # a delivered result releases its ticket
