@@ -10,17 +10,18 @@
 // broadcast), and the next tile streams into the other shared-memory buffer with cp.async while
 // the current one is used.
 //
-// Per tile (NW warps; SH = TS / 32 sample halves, KS = NW / SH feature splits):
+// Per tile (NW warps; SH = TS / 32 groups of 32 samples, KS = NW / SH feature splits):
 //   phase 1  Z = V_t A          warp w: samples [32 (w % SH), +32), features of split w / SH;
 //                               lane: samples g, g+8, g+16, g+24 (g = lane / 4) x columns
 //                               4 (lane % 4) .. +3; the KS split partials go to shared memory
 //   weights  z = sum of the KS split partials (fixed order); W = nu z^{d-1}; w += nu z^d
 //   phase 2  Y += V_t^T W       warp: 32 features (lane: 4 features x 4 columns) over its share
 //                               of the tile's samples (warps split the samples when n is small)
-// Each phase ends at a block barrier. The pass runs 32-sample tiles with 8 warps and two blocks
-// per SM, so that one block's barrier waits overlap the other block's arithmetic (measured
-// against 64-sample tiles with 16 warps and one block per SM: 8.6 against 9.4 ms at n = 256,
-// r = 16, p = 2^24, and 0.80 against 1.13 ms at n = 100, r = 10, p = 2.5e6).
+// Each phase ends at a block barrier. The pass runs 8 warps and two blocks per SM, so that one
+// block's barrier waits overlap the other block's arithmetic (measured against 64-sample tiles
+// with 16 warps and one block per SM: 8.6 against 9.4 ms at n = 256, r = 16, p = 2^24, and 0.80
+// against 1.13 ms at n = 100, r = 10, p = 2.5e6). The tile grows as n shrinks (32 samples for
+// n > 128, 64 for n > 64, 128 otherwise), so that each barrier covers the same work per thread.
 // Y is folded from FP32 into the block's FP64 partial and w into FP64 registers every
 // 64 flush_tiles samples, in a fixed order (results reproducible bit for bit).
 #include <cuda_runtime.h>
@@ -31,25 +32,28 @@ namespace stmf {
 namespace {
 
 constexpr int RC = 16;  // columns of A handled (r <= 16, zero-padded)
-constexpr int KS = 8;   // phase 1: K splits (NW / (TS / 32))
 
-// TS samples per tile, NW warps per block, MB blocks per SM
-template <int TS_, int NW_, int MB_>
+// TS samples per tile, NW warps per block, MB blocks per SM, for n <= NMAX
+template <int TS_, int NW_, int MB_, int NMAX_>
 struct Cfg {
+  static constexpr int NMAX = NMAX_;
   static constexpr int TS = TS_;
   static constexpr int NW = NW_;
   static constexpr int MB = MB_;
   static constexpr int NT = 32 * NW;
-  static constexpr int SH = TS / 32;         // phase 1: sample halves of 32
+  static constexpr int SH = TS / 32;         // phase 1: groups of 32 samples
+  static constexpr int KS = NW / SH;         // phase 1: K splits
   static constexpr int EPT = TS * RC / NT;   // weights: (sample, column) entries per thread
   static constexpr int CPT = RC / EPT;       // weights: threads per sample
-  static_assert(NW / SH == KS, "phase 1 splits the features KS ways");
+  static_assert(KS * SH == NW && KS >= 1, "phase 1 splits the features KS ways");
   static_assert(NT == TS * CPT, "one weights thread per (sample, column group)");
 };
-using CfgPair = Cfg<32, 8, 2>;
+using CfgN256 = Cfg<32, 8, 2, 256>;   // 128 < n <= 256
+using CfgN128 = Cfg<64, 8, 2, 128>;   //  64 < n <= 128
+using CfgN64 = Cfg<128, 8, 2, 64>;    //       n <= 64
 
 struct Shape {
-  int np;      // features padded to a multiple of 4 KS (each K split a multiple of 4)
+  int np;      // features padded to a multiple of 32 (each K split a multiple of 4)
   int pitch;   // floats between consecutive samples in shared memory (np + 4: odd 16-byte count)
   int kq;      // features per K split in phase 1 (np / KS)
   int p2;      // feature warps in phase 2 (power of two >= ceil(np / 32))
@@ -59,9 +63,9 @@ struct Shape {
 template <class C>
 Shape shape_of(int n) {
   Shape s;
-  s.np = (n + 4 * KS - 1) / (4 * KS) * (4 * KS);
+  s.np = (n + 31) / 32 * 32;
   s.pitch = s.np + 4;
-  s.kq = s.np / KS;
+  s.kq = s.np / C::KS;
   const int nfb = (s.np + 31) / 32;
   s.p2 = 1;
   while (s.p2 < nfb) s.p2 <<= 1;
@@ -74,7 +78,7 @@ size_t smem_of(const Shape& s) {
   constexpr int TS = C::TS;
   return sizeof(float) * (2 * size_t(TS) * s.pitch  // V tiles (double buffer)
                           + size_t(s.np) * RC       // A
-                          + KS * TS * RC            // K-split partials of Z (reused at the end)
+                          + C::KS * TS * RC         // K-split partials of Z (reused at the end)
                           + TS * RC)                // W
          + sizeof(double) * 2 * TS;                 // nu (double buffer)
 }
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(C::NT, C::MB) fg_f32_kernel(const FgParams prm
   float* Vs = reinterpret_cast<float*>(smem_raw);
   float* As = Vs + 2 * TS * sh.pitch;
   float* Zp = As + sh.np * RC;
-  float* Ws = Zp + KS * TS * RC;
+  float* Ws = Zp + C::KS * TS * RC;
   double* nus = reinterpret_cast<double*>(Ws + TS * RC);
 
   const int n = prm.n, r = prm.r, d = prm.d;
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(C::NT, C::MB) fg_f32_kernel(const FgParams prm
   for (int a = 0; a < 4; ++a) yacc[a][0] = yacc[a][1] = make_float2(0.f, 0.f);
   bool first_flush = true;
 
-  const int flush_every = prm.flush_tiles * (64 / TS);
+  const int flush_every = (prm.flush_tiles * 64 + TS - 1) / TS;  // every 64 flush_tiles samples
   if (my_tiles > 0) stage_tile<C>(prm, sh, walk, Vs, nus, blockIdx.x);
   cp_async_commit();
   int since_flush = 0;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(C::NT, C::MB) fg_f32_kernel(const FgParams prm
 #pragma unroll
       for (int c = 0; c < EPT; ++c) z[c] = 0.f;
 #pragma unroll
-      for (int q = 0; q < KS; ++q) {  // K splits added in order
+      for (int q = 0; q < C::KS; ++q) {  // K splits added in order
         const float* zp = Zp + (q * TS + sw) * RC + EPT * cw;
 #pragma unroll
         for (int c = 0; c < EPT; ++c) z[c] += zp[c];
@@ -363,17 +367,23 @@ template <class C>
 cudaError_t launch_cfg(const FgParams& prm, int grid, cudaStream_t s) {
   const Shape sh = shape_of<C>(prm.n);
   const size_t smem = smem_of<C>(sh);
-  const cudaError_t e = smem_limit((const void*)fg_f32_kernel<C>, int(smem_of<C>(shape_of<C>(256))));
+  const cudaError_t e = smem_limit((const void*)fg_f32_kernel<C>, int(smem_of<C>(shape_of<C>(C::NMAX))));
   if (e != cudaSuccess) return e;
   return launch_kernel(fg_f32_kernel<C>, dim3(grid), dim3(C::NT), smem, s, prm, sh);
 }
 
 }  // namespace
 
-int fg_f32_grid(int, int64_t p, int num_sms) { return grid_of<CfgPair>(p, num_sms); }
+int fg_f32_grid(int n, int64_t p, int num_sms) {
+  return n > 128  ? grid_of<CfgN256>(p, num_sms)
+         : n > 64 ? grid_of<CfgN128>(p, num_sms)
+                  : grid_of<CfgN64>(p, num_sms);
+}
 
 cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s) {
-  return launch_cfg<CfgPair>(prm, grid, s);
+  return prm.n > 128  ? launch_cfg<CfgN256>(prm, grid, s)
+         : prm.n > 64 ? launch_cfg<CfgN128>(prm, grid, s)
+                      : launch_cfg<CfgN64>(prm, grid, s);
 }
 
 }  // namespace stmf

@@ -78,6 +78,9 @@ SHAPES = [
     (64, 5000, 8, 3),
     (100, 20000, 10, 3),
     (100, 20000, 10, 4),
+    (65, 777, 7, 4),      # just past 64 features, and 128 / 129: the FP32 pass's tile changes
+    (128, 4099, 16, 3),
+    (129, 2001, 16, 3),
     (256, 70000, 16, 4),
     (128, 3000, 64, 2),   # r at its maximum, the matrix case
     (256, 300, 33, 5),
