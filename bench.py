@@ -198,25 +198,19 @@ def make_requests(count, seed, dev):
     return out
 
 
-def serving_bench(n_requests, seed, dev, device_index):
+def serving_bench(n_requests, seed, dev, device_index, sweep=()):
     """Continuous batching through stmf_server_*: a saturated run fixes the capacity, then Poisson
-    arrivals at 0.8x that rate give the latency percentiles."""
+    arrivals at 0.8x that rate give the latency percentiles; `sweep` lists further multiples of
+    the saturated rate, each run on the same requests with its own arrival draw."""
     import numpy as np
 
     from paper_1911_03813_gb300 import stmf
     opts = dict(pgtol=1e-5, factr=1e9, max_evals=200, alpha_mode=0, chunk=8)
     sat = make_requests(max(n_requests // 2, 8), seed, dev)
     poi = make_requests(n_requests, seed + 1, dev)
-    with stmf.Server(device=device_index, max_fits=64, n_max=128, r_max=16, m_max=5,
-                     mem_budget=150 << 30) as srv:
-        t0 = time.perf_counter()
-        tick = [srv.submit(q["V"], q["d"], q["x0"], **opts) for q in sat]
-        res = [srv.poll(t) for t in tick]
-        t_sat = time.perf_counter() - t0
-        ok_sat = sum(r_["state"] == 0 for r_ in res)
-        rate_sat = len(sat) / t_sat
-        rate = 0.8 * rate_sat
-        gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, size=len(poi))
+
+    def poisson(srv, rate, draw_seed):
+        gaps = np.random.default_rng(draw_seed).exponential(1.0 / rate, size=len(poi))
         t0 = time.perf_counter()
         due = t0
         tick = []
@@ -226,18 +220,37 @@ def serving_bench(n_requests, seed, dev, device_index):
                 time.sleep(0.0002)
             tick.append(srv.submit(q["V"], q["d"], q["x0"], **opts))
         res = [srv.poll(t) for t in tick]
-        t_poi = time.perf_counter() - t0
+        el = time.perf_counter() - t0
+        lat = np.array([r_["t_done"] - r_["t_submit"] for r_ in res]) * 1e3
+        return {"arrival_rate_per_s": rate, "fits_per_s": 4 * len(poi) / el,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "completed": int(sum(r_["state"] == 0 for r_ in res))}
+
+    with stmf.Server(device=device_index, max_fits=64, n_max=128, r_max=16, m_max=5,
+                     mem_budget=150 << 30) as srv:
+        t0 = time.perf_counter()
+        tick = [srv.submit(q["V"], q["d"], q["x0"], **opts) for q in sat]
+        for t in tick:
+            srv.poll(t)
+        t_sat = time.perf_counter() - t0
+        rate_sat = len(sat) / t_sat
+        main = poisson(srv, 0.8 * rate_sat, seed + 2)
+        extra = []
+        for k, mult in enumerate(sweep):
+            row = poisson(srv, mult * rate_sat, seed + 3 + k)
+            row["rate_over_saturated"] = mult
+            extra.append(row)
         stats = srv.stats()
-    lat = np.array([r_["t_done"] - r_["t_submit"] for r_ in res]) * 1e3
-    return {"requests": len(poi), "starts_per_request": 4,
-            "workload": "n, p log-uniform in [8,128] x [1e3,1e6], d in {3,4}, r in [1,16], "
-                        "sigma log-uniform in [1e-4,1e-1], BF16 samples on the host",
-            "saturated_requests_per_s": rate_sat, "saturated_fits_per_s": 4 * rate_sat,
-            "arrival_rate_per_s": rate, "fits_per_s": 4 * len(poi) / t_poi,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "completed": int(sum(r_["state"] == 0 for r_ in res)) + 0 * ok_sat,
-            "peak_admitted_bytes": int(stats["peak_bytes_in_use"]),
-            "optimiser": "L-BFGS m=5, pgtol 1e-5, factr 1e9, <= 200 evaluations per start"}
+    out = {"requests": len(poi), "starts_per_request": 4,
+           "workload": "n, p log-uniform in [8,128] x [1e3,1e6], d in {3,4}, r in [1,16], "
+                       "sigma log-uniform in [1e-4,1e-1], BF16 samples on the host",
+           "saturated_requests_per_s": rate_sat, "saturated_fits_per_s": 4 * rate_sat,
+           **main,
+           "peak_admitted_bytes": int(stats["peak_bytes_in_use"]),
+           "optimiser": "L-BFGS m=5, pgtol 1e-5, factr 1e9, <= 200 evaluations per start"}
+    if extra:
+        out["sweep"] = extra
+    return out
 
 
 def gram_bench(dev):
@@ -410,6 +423,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep_of(args):
+    return tuple(float(x) for x in args.serving_sweep.split(",") if x.strip())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +438,11 @@ def main():
     ap.add_argument("--p", type=int, default=P_FULL)
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--no-gram", action="store_true")
+    ap.add_argument("--serving-sweep", default="",
+                    help="comma-separated multiples of the saturated serving rate to run after "
+                         "the 0.8x run (e.g. 0.5,1.0,1.2)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving workload (its JSON object on one line)")
     ap.add_argument("--gmm-study", action="store_true",
                     help="run the Gaussian-mixture study grid of Sec. 4.2 (n=500) and print its line")
     ap.add_argument("--alpha-only", action="store_true",
@@ -449,6 +471,10 @@ def main():
         return
     if args.alpha_only:
         print(json.dumps(alpha_bench(dev)), flush=True)
+        return
+    if args.serving_only:
+        print(json.dumps(serving_bench(max(args.serving_requests, 8), SEED, dev, local,
+                                       sweep_of(args))), flush=True)
         return
     if args.gmm_study:
         from paper_1911_03813_gb300 import study
@@ -601,7 +627,8 @@ def main():
     alpha = None if args.no_gram else alpha_bench(dev)
     fp32_scale = None if args.no_gram else fp32_scale_bench(dev)
     differentiation = None if args.no_gram else autograd_bench(dev)
-    serving = serving_bench(args.serving_requests, SEED, dev, local) if args.serving_requests else None
+    serving = (serving_bench(args.serving_requests, SEED, dev, local, sweep_of(args))
+               if args.serving_requests else None)
     cpu = None if args.no_cpu_baseline else cpu_baseline(dev)
     traffic = ncu_traffic("fg_pass_bf16")
     line = {
