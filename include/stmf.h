@@ -117,18 +117,18 @@ STMF_API stmf_status stmf_device_status(stmf_ctx_t ctx, stmf_stream_t stream, in
 
 /*
  * stmf_fg -- function value and gradient by Alg. 2 (fg_implicit, Sec. 3.4):
- *     Y   = V D_nu [V^T A]^{d-1}            (line 2, Lemma 3.3, eq. Y)
- *     w_j = a_j^T y_j                       (line 3, Lemma 3.5: <X, M> = w^T lambda)
- *     B = A^T A, C = B^{d-1}, u = (B * C) lambda   (lines 4-6, Lemma 3.4: ||M||^2 = lambda^T u)
- *     f   = alpha + lambda^T u - 2 w^T lambda     (line 7)
- *     g_lambda = -2 (w - u)                        (line 8, eq. gradl)
- *     G_A = -2 d (Y - A D_lambda C) D_lambda       (line 9, eq. gradb)
+ *     Y   = V D_nu [V^T A]^{d-1}            (Lemma 3.3, eq. Y)
+ *     w_j = a_j^T y_j                       (Lemma 3.5: <X, M> = w^T lambda)
+ *     B = A^T A, C = B^{d-1}, u = (B * C) lambda   (Lemma 3.4: ||M||^2 = lambda^T u)
+ *     f   = alpha + lambda^T u - 2 w^T lambda     (eq. optFunc expanded)
+ *     g_lambda = -2 (w - u)                        (eq. gradl)
+ *     G_A = -2 d (Y - A D_lambda C) D_lambda       (eq. gradb)
  * Powers of matrices are element-wise (Sec. 2).
  *
  *  V        samples (see stmf_samples). BF16 and E4M3 samples are contracted on the tensor
  *           cores with FP32 accumulation (n <= 256, r <= 16); F32 with FP32 FMA; F64 with FP64
  *           FMA; other shapes on the CUDA cores in FP32 (FP64 for F64). Per-block partial sums
- *           are combined in FP64 and lines 3-9 run in FP64. The CUDA-core pass stages 64
+ *           are combined in FP64 and every step after Y runs in FP64. The CUDA-core pass stages 64
  *           samples in shared memory and holds Y in registers: it needs n x ceil4(r) <= 16384
  *           and 64 (n + 1) elements plus n x ceil4(r) of the compute type (FP32, or FP64 for
  *           F64 samples) within 227 KB; outside that the call returns STMF_EINVAL (for example
@@ -154,7 +154,7 @@ STMF_API stmf_status stmf_fg(stmf_ctx_t ctx, const stmf_samples* V, const double
  * previous ones; chunk partials are summed in FP64 in chunk order; f, g_lambda and G_A are
  * copied back. Use pinned host memory for V: from pageable memory the copies do not overlap.
  *  V        host samples (stmf_samples with host pointers).   nu  host p FP64 or NULL (1/p).
- *  lambda   host r.   A  host n x r column-major.   alpha  the constant of line 7 (0: shifted).
+ *  lambda   host r.   A  host n x r column-major.   alpha  the constant ||X||^2 of f (0: shifted).
  *  f, g_lambda, G_A   host outputs.
  * Synchronous: returns when the outputs are in host memory. The first call, and a call with
  * larger rows than before, allocates the staging buffers (synchronising the device).
@@ -167,14 +167,14 @@ STMF_API stmf_status stmf_fg_host(stmf_ctx_t ctx, const stmf_samples* V, const d
 /*
  * Sample-sharded evaluation. Every sum of Alg. 2 over samples (eq. Y, Lemma 3.5) splits over
  * disjoint shards of V, so G devices holding shards V_g each compute their partial (w, Y), the
- * partials are summed (one all-reduce of r + n r FP64 values), and lines 4-9 follow:
+ * partials are summed (one all-reduce of r + n r FP64 values), and the model terms follow:
  *
  * stmf_fg_partial -- yw = [w; vec(Y)] summed over this shard: w_j = sum_l nu_l (v_l^T a_j)^d,
  *   Y = sum_l nu_l (v_l^T A)^{d-1} v_l^T (n x r column-major after the r entries of w).
  *   nu       device weights of this shard's samples, or NULL for nu_l = 1 / p_total.
  *   p_total  the number of samples over all shards (used when nu is NULL; >= V->p).
  *   yw       device, r + n r FP64 (out).
- * stmf_fg_finish -- f, g_lambda, G_A from a summed yw (lines 4-9: B = A^T A, C, u, f, g).
+ * stmf_fg_finish -- f, g_lambda, G_A from a summed yw (B = A^T A, C, u, then f and the gradients).
  *   n        features.   Other arguments as for stmf_fg.
  * Both enqueue on `stream`; asynchronous.
  */

@@ -85,7 +85,7 @@ def grad_bruteforce(X, lam, A):
 
 
 def fg_explicit(X, lam, A, alpha=0.0):
-    """Alg. 1 (fg_explicit, Sec. 3.4): the TTSVs of line 2 are taken on the explicit X.
+    """Alg. 1 (fg_explicit, Sec. 3.4): the TTSVs y_j = X a_j^{d-1} are taken on the explicit X.
 
     Returns (f, g_lambda, G_A)."""
     d = X.ndim
@@ -93,15 +93,15 @@ def fg_explicit(X, lam, A, alpha=0.0):
     lam = np.asarray(lam, dtype=np.float64)
     n, r = A.shape
     Y = np.empty((n, r))
-    for j in range(r):                      # line 2: y_j = X a_j^{d-1}
+    for j in range(r):                      # y_j = X a_j^{d-1}
         Y[:, j] = ttsv_but_one(X, A[:, j])
-    w = np.array([A[:, j] @ Y[:, j] for j in range(r)])   # line 3
-    B = A.T @ A                             # line 4
-    C = B ** (d - 1)                        # line 5
-    u = (B * C) @ lam                       # line 6
-    f = alpha + lam @ u - 2.0 * (w @ lam)   # line 7
-    g_lam = -2.0 * (w - u)                  # line 8
-    G_A = -2.0 * d * (Y - A @ np.diag(lam) @ C) @ np.diag(lam)   # line 9
+    w = np.array([A[:, j] @ Y[:, j] for j in range(r)])   # w_j = a_j^T y_j
+    B = A.T @ A
+    C = B ** (d - 1)                        # element-wise power
+    u = (B * C) @ lam                       # lambda^T u = ||M||^2
+    f = alpha + lam @ u - 2.0 * (w @ lam)
+    g_lam = -2.0 * (w - u)                  # eq. gradl
+    G_A = -2.0 * d * (Y - A @ np.diag(lam) @ C) @ np.diag(lam)   # eq. gradb
     return float(f), g_lam, G_A
 
 

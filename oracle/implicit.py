@@ -49,21 +49,21 @@ def fg_implicit(nu, V, lam, A, d, alpha=0.0, p=None, chunk=DEFAULT_CHUNK, return
 
     Returns (f, g_lambda, G_A), and with return_parts=True also a dict of the intermediate
     quantities Y, w, B, C, u (for parity checks of the GPU path's pieces)."""
-    Y = ttsv_matrix(nu, V, _as_f64(A), d, p=p, chunk=chunk)  # line 2
+    Y = ttsv_matrix(nu, V, _as_f64(A), d, p=p, chunk=chunk)  # eq. Y
     return model_terms(Y, lam, A, d, alpha=alpha, return_parts=return_parts)
 
 
 def model_terms(Y, lam, A, d, alpha=0.0, return_parts=False):
-    """Alg. 2 lines 3-9 from Y (line 2): w, B, C, u, then f, g_lambda and G_A."""
+    """The steps of Alg. 2 after Y: w, B, C, u, then f, g_lambda and G_A."""
     lam = _as_f64(lam)
     A = _as_f64(A)
-    w = np.einsum("ij,ij->j", A, Y)                         # line 3: w_j = a_j^T y_j
-    B = A.T @ A                                             # line 4
-    C = B ** (d - 1)                                        # line 5
-    u = (B * C) @ lam                                       # line 6
-    f = alpha + lam @ u - 2.0 * (w @ lam)                   # line 7
-    g_lam = -2.0 * (w - u)                                  # line 8
-    G_A = -2.0 * d * (Y - A @ np.diag(lam) @ C) @ np.diag(lam)   # line 9
+    w = np.einsum("ij,ij->j", A, Y)                         # w_j = a_j^T y_j
+    B = A.T @ A
+    C = B ** (d - 1)                                        # element-wise power
+    u = (B * C) @ lam                                       # lambda^T u = ||M||^2
+    f = alpha + lam @ u - 2.0 * (w @ lam)
+    g_lam = -2.0 * (w - u)                                  # eq. gradl
+    G_A = -2.0 * d * (Y - A @ np.diag(lam) @ C) @ np.diag(lam)   # eq. gradb
     if return_parts:
         return float(f), g_lam, G_A, dict(Y=Y, w=w, B=B, C=C, u=u)
     return float(f), g_lam, G_A

@@ -1,7 +1,7 @@
 // Fused pass over FP32 samples on the CUDA cores, register-blocked (r <= 16, n <= 256).
 //
 // Per persistent block and over that block's tiles of TS samples it accumulates the partial
-// sums of Alg. 2 line 2 (Lemma 3.3, eq. Y) and Lemma 3.5:
+// sums of Alg. 2's Y (Lemma 3.3, eq. Y) and of Lemma 3.5:
 //     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
 // reading every sample from HBM once. The arithmetic is 2 n r FMA per sample per product (Z = V A
 // and Y += V^T W); at n = 256, r = 16 that is above the HBM time of the FP32 samples, so the

@@ -8,7 +8,7 @@
 //
 // One persistent block walks sample tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... and
 // accumulates, for its tiles only,
-//     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l^T      (Alg. 2 line 2, Lemma 3.3, eq. Y)
+//     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l^T      (Alg. 2, Lemma 3.3, eq. Y)
 //     w_part = sum_l nu_l (v_l^T A)^d                (Lemma 3.5: w_j = X a_j^d = a_j^T y_j)
 // Each tile is staged in shared memory once and used twice: phase 1 forms Z = V_tile A and the
 // weighted powers W = D_nu Z^{d-1}; phase 2 adds V_tile^T W into register accumulators. FP32

@@ -1,7 +1,7 @@
 // Fused pass over BF16 samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM).
 //
-// Computes, per persistent CTA and over that CTA's sample tiles, the partial sums of Alg. 2
-// line 2 (Lemma 3.3, eq. Y) and of Lemma 3.5:
+// Computes, per persistent CTA and over that CTA's sample tiles, the partial sums of Alg. 2's
+// Y (Lemma 3.3, eq. Y) and of Lemma 3.5:
 //     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
 // reading every sample from HBM exactly once.
 //

@@ -1,13 +1,13 @@
-// Model terms and outputs of Alg. 2 (lines 3-9), in FP64.
+// Model terms and outputs of Alg. 2 (every step after Y), in FP64.
 //
 // reduce_kernel:   (w, Y) = sum over the pass's blocks of their FP64 partials (16 threads per
 //                  entry, combined in a fixed order, so results are reproducible bit for bit),
-//                  and, in extra blocks, B = A^T A (Alg. 2 line 4), one warp per entry.
-// finalize_kernel: C = B^{d-1} (line 5), then one thread per entry of
-//                  G_A = -2 d (Y - A D_lambda C) D_lambda (line 9, eq. gradb); block 0 also forms
-//                  u = (B * C) lambda (line 6, Lemma 3.4), f = alpha + lambda^T u - 2 w^T lambda
-//                  (line 7) and g_lambda = -2 (w - u) (line 8, eq. gradl). The two inner products
-//                  of line 7 are summed by one thread in index order.
+//                  and, in extra blocks, B = A^T A (Alg. 2), one warp per entry.
+// finalize_kernel: C = B^{d-1} (element-wise), then one thread per entry of
+//                  G_A = -2 d (Y - A D_lambda C) D_lambda (eq. gradb); block 0 also forms
+//                  u = (B * C) lambda (Lemma 3.4), f = alpha + lambda^T u - 2 w^T lambda
+//                  and g_lambda = -2 (w - u) (eq. gradl). The two inner products of f are
+//                  summed by one thread in index order.
 #include "stmf_internal.h"
 
 namespace stmf {

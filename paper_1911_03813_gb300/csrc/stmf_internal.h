@@ -11,7 +11,7 @@
 
 namespace stmf {
 
-// Launch parameters of the fused pass over V (Alg. 2 line 2 plus the sum of line 3).
+// Launch parameters of the fused pass over V (Alg. 2: Y, and the sums behind w).
 struct FgParams {
   const void* V;        // sample-major storage, p rows of ld elements
   const float* scale;   // per-sample scales (e4m3) or nullptr
@@ -30,7 +30,7 @@ struct FgParams {
   uint64_t seed;        // randomized range finder: key of the Philox test matrix
 };
 
-// Finalisation of Alg. 2 lines 3-9 from the reduced (w, Y).
+// Finalisation of Alg. 2 (the steps after Y) from the reduced (w, Y).
 struct ModelParams {
   const double* partials;  // [grid][L] with L = r + n*r
   int grid;
@@ -94,7 +94,7 @@ int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s, bool f64);
 // Sum the block partials only (no model terms): yw = sum_g partials[g].
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
-// Alg. 2 lines 4-9 from a given yw = [w; vec(Y)] (B = A^T A, then the outputs).
+// Alg. 2 from a given yw = [w; vec(Y)] (B = A^T A, then the outputs).
 cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s);
 // Register-blocked CUDA-core pass for FP32 samples (n <= 256, r <= 16; gathers supported).
 bool fg_f32_supported(int dtype, int n, int r);

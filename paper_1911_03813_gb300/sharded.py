@@ -2,7 +2,7 @@
 
 Every sum over samples in Alg. 2 (eq. Y, Lemma 3.5) splits over disjoint shards of V. Each rank
 holds its shard, computes its partial [w; vec(Y)] (stmf_fg_partial, with nu = 1 / p_total), the
-partials are summed by one all-reduce of r + n r FP64 values, and every rank finishes lines 4-9
+partials are summed by one all-reduce of r + n r FP64 values, and every rank finishes the model terms
 (stmf_fg_finish) on the summed values. The partial and finish steps are parameters so that the
 same orchestration can be exercised with other implementations of the two steps.
 """
