@@ -246,7 +246,7 @@ typedef struct {
   double alpha;      /* ||X||^2 when alpha_mode = 1, else 0 */
   double g_inf;      /* max |g_i| at the returned iterate */
   int64_t iters;     /* outer iterations */
-  int64_t evals;     /* function/gradient evaluations ("inner iterations", Sec. 4.1) */
+  int64_t evals;     /* function/gradient evaluations (the inner iterations of Sec. 4.1) */
   int32_t stop_reason;
   int32_t status;
 } stmf_fit_result;

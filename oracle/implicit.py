@@ -5,7 +5,7 @@ taken in chunks of columns only to bound host memory, which changes no arithmeti
 algorithm (Y is a sum over samples, eq. Y).
 
 Orientation follows the paper: V is n x p (one sample per column), A is n x r, nu has p
-positive entries (Sec. 3: "arbitrary positive nu").
+positive entries (Sec. 3 allows any positive weights).
 """
 
 import numpy as np
@@ -97,6 +97,6 @@ def norm_x(nu, V, d, p=None, chunk=4096):
 
 def relative_error(f, alpha):
     """||X - M|| / ||X|| from the implicit objective: sqrt(max(f, 0) / alpha), with f computed
-    with alpha = ||X||^2 (Sec. 4.2 computes the error "from observed data" with Sec. 3.3's
+    with alpha = ||X||^2 (Sec. 4.2 obtains the error from the data alone through Sec. 3.3's
     terms; this is that reading)."""
     return float(np.sqrt(max(f, 0.0) / alpha))

@@ -2,8 +2,8 @@
 
 Test infrastructure only (see the package docstring).
 
-Sec. 4 runs L-BFGS-B with no bounds, memory m = 5, "maximum iterations = 10,000; maximum total
-iterations = 50,000" and a gradient tolerance pgtol. With infinite bounds the projected gradient
+Sec. 4 runs L-BFGS-B with no bounds, memory m = 5, caps of 10,000 outer and 50,000 total
+iterations, and a gradient tolerance pgtol. With infinite bounds the projected gradient
 is the gradient, so the method is plain L-BFGS. The paper does not list the other settings; the
 readings used here (and by the device optimiser, which follows the same steps) are:
 
@@ -16,7 +16,7 @@ readings used here (and by the device optimiser, which follows the same steps) a
     at step 1; at most `max_ls` evaluations per line search;
   * stopping: ||g||_inf <= pgtol; relative decrease (f_k - f_{k+1}) / max(|f_k|, |f_{k+1}|, 1)
     <= factr * eps (factr = 1e7); `max_iters` outer iterations; `max_evals` evaluations
-    ("total iterations", i.e. calls of the function/gradient, Sec. 4.1);
+    (Sec. 4.1's total iterations, i.e. calls of the function/gradient);
   * a pair (s, y) is stored only when s^T y > 1e-10 * y^T y (positive curvature).
 
 Stop reasons: 1 pgtol, 2 factr, 3 max_iters, 4 max_evals, 5 line search failed, 6 non-finite.

@@ -30,8 +30,8 @@ def adam(V, lam0, A0, d, sample_idx, est_idx, lr0=1e-2, lr1=1e-3, epoch=100,
       the state returns to the end of the prior epoch; the second time, the method stops and
       returns the prior epoch's iterate.
 
-    Reading where Sec. 5 is silent: "returns to the iterate from the prior epoch" restores the
-    Adam moments and step counter of that epoch as well as (lambda, A).
+    Reading where Sec. 5 is silent: going back to the prior epoch's iterate restores that
+    epoch's Adam moments and step counter as well as (lambda, A).
 
     Returns dict(lam, A, f_est, epochs, trace)."""
     lam = np.array(lam0, dtype=np.float64)
