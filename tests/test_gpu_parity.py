@@ -78,9 +78,6 @@ SHAPES = [
     (64, 5000, 8, 3),
     (100, 20000, 10, 3),
     (100, 20000, 10, 4),
-    (65, 777, 7, 4),      # just past 64 features, and 128 / 129: the FP32 pass's tile changes
-    (128, 4099, 16, 3),
-    (129, 2001, 16, 3),
     (256, 70000, 16, 4),
     (128, 3000, 64, 2),   # r at its maximum, the matrix case
     (256, 300, 33, 5),
@@ -96,6 +93,17 @@ def test_fg_parity(stmf, dtype, n, p, r, d):
     lam, A = inputs.random_model(n, r, seed=3 * r + d)
     st = inputs.to_storage(data["V"], dtype, device="cuda")
     check_fg(stmf, st, None, lam, A, d, TOL[dtype])
+
+
+@pytest.mark.parametrize("n,p,r,d", [(64, 777, 7, 4), (65, 777, 7, 4), (128, 4099, 16, 3),
+                                     (129, 2001, 16, 3)])
+def test_fg_f32_tile_boundaries(stmf, n, p, r, d):
+    """The FP32 pass takes 128-sample tiles up to n = 64, 64-sample tiles up to n = 128 and
+    32-sample tiles above: both sides of each boundary, with ragged tails."""
+    data = inputs.gmm(n, p, min(r, 8), 0.1, seed=n + p + r + d)
+    lam, A = inputs.random_model(n, r, seed=3 * r + d)
+    st = inputs.to_storage(data["V"], "f32", device="cuda")
+    check_fg(stmf, st, None, lam, A, d, TOL["f32"])
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
