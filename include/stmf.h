@@ -325,6 +325,8 @@ typedef struct {
   size_t peak_bytes_in_use;
   size_t slot_bytes;       /* preallocated slot workspaces */
   double now;              /* server clock, seconds */
+  int32_t peak_active_fits; /* most fits that held a slot at the same time since creation */
+  int32_t reserved;
 } stmf_server_stats;
 
 /* Create a server: allocates max_fits slots (fails with STMF_ENOMEM when they alone exceed
@@ -441,14 +443,22 @@ STMF_API stmf_status stmf_adam(stmf_ctx_t ctx, const stmf_samples* V, int32_t d,
  * scratch (a request outside them returns STMF_EINVAL before any work; STMF_ENOMEM would mean
  * the scratch cannot hold two blocks' partials, which no valid n, r reaches).
  *
- * All calls on a device share the array and leave their contents in it; each call overwrites
- * every partial it reads and clears the status word it uses. Calls whose work overlaps on the
- * GPU (other streams or host threads) race on the array: serialise them.
+ * All calls on a device share the array and leave their contents in it. A call writes every
+ * block partial it reads unless a block of its pass gave up on a bounded wait; such a block
+ * records STMF_ETIMEOUT in the status word, and whenever the status word is nonzero by the time
+ * the model terms run, f, g_lambda and G_A are written as NaN instead of a result, so partials
+ * left by an earlier call never reach an output. Calls whose work overlaps on the GPU (other
+ * streams or host threads) race on the array: serialise them. The cached address of the array
+ * is looked up again on every call whose stream is not capturing (so a cudaDeviceReset between
+ * calls is harmless); a call on a capturing stream returns STMF_EINVAL if no earlier call on
+ * this device cached it.
  *
  *  V, nu, d, r, lambda, A, alpha, f, g_lambda, G_A   as for stmf_fg (device pointers).
  *  status   device, 1 int32 owned by the caller, or NULL. When given, device-side errors
- *           (e.g. STMF_ENONFINITE) are written there (the caller clears it); when NULL they go
- *           to a word inside the scratch that the call clears first.
+ *           (STMF_ENONFINITE, STMF_ETIMEOUT) are recorded there; the call does not clear it,
+ *           so a word still holding an earlier error also makes the outputs NaN. When NULL,
+ *           errors go to a word inside the scratch that the call clears first, and the NaN
+ *           outputs are the only sign of them.
  * Enqueued on `stream`; asynchronous; the current device must be the device of all pointers.
  */
 STMF_API stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, int32_t d, int64_t r,

@@ -11,14 +11,18 @@
 // process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the device address of
-// the array with cudaGetSymbolAddress and caches it; make that first call before any stream
-// capture. The call itself allocates nothing and frees nothing.
+// the array with cudaGetSymbolAddress; make that first call before any stream capture. Later
+// calls look it up again whenever their stream is not capturing (the lookup is cheap and stays
+// correct after a cudaDeviceReset reloads the module); a call on a capturing stream uses the
+// address cached by the last call on that device. The call itself allocates nothing and frees
+// nothing.
 //
-// Sharing: every call on a device uses the same array and leaves its contents behind. The
-// kernels overwrite every partial they later read, and the call clears the status word it uses,
-// so nothing from an earlier call leaks into a result. Two calls whose work overlaps on the GPU
-// (different streams, or different host threads) race on the array and give wrong results:
-// serialise them.
+// Sharing: every call on a device uses the same array and leaves its contents behind. A call
+// writes every block partial it reads, unless a block gave up on a bounded wait; in that case
+// it has set an error in the status word, and the model-terms kernel then writes NaN to f,
+// g_lambda and G_A rather than a result built from another call's partials. Two calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on the array and give
+// wrong results: serialise them.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,11 +40,14 @@ static __device__ __align__(256) double g_fg_scratch[kScratchDoubles + 32];
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
 
-stmf_status scratch_for_current_device(double** out) {
+stmf_status scratch_for_current_device(cudaStream_t stream, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return STMF_ECUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return STMF_ECUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone) return STMF_EINVAL;  // no address cached yet
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_fg_scratch);
     if (e != cudaSuccess || !p) return STMF_ECUDA;
@@ -56,14 +63,8 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
                                        int64_t r, const double* lambda, const double* A,
                                        const double* alpha, double* f, double* g_lambda,
                                        double* G_A, int32_t* status, stmf_stream_t stream) {
-  // argument checks (the same rules as stmf_fg)
-  if (!V || !V->data) return STMF_EINVAL;
-  const int eb = stmf::elem_bytes(V->dtype);
-  if (eb == 0 || V->n < 1 || V->n > 512 || V->p < 1 || V->p > (int64_t(1) << 40) ||
-      V->ld < V->n || (V->ld * eb) % 16 != 0 ||
-      (reinterpret_cast<uintptr_t>(V->data) & 15) != 0)
-    return STMF_EINVAL;
-  if ((V->dtype == STMF_E4M3) != (V->scale != nullptr)) return STMF_EINVAL;
+  // argument checks (the same rules, limits and messages as stmf_fg)
+  if (stmf::samples_problem(V)) return STMF_EINVAL;
   if (d < 2 || d > 8 || r < 1 || r > 64) return STMF_EINVAL;
   if (!lambda || !A || !f || !g_lambda || !G_A) return STMF_EINVAL;
 
@@ -78,7 +79,7 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   const int n = (int)V->n;
   const bool tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
   const bool f32 = !tc && stmf::fg_f32_supported(V->dtype, n, (int)r);
-  if (!tc && !f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > 232448) return STMF_EINVAL;
+  if (!tc && !f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > stmf::kMaxSmem) return STMF_EINVAL;
   int grid = tc    ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, sms)
              : f32 ? stmf::fg_f32_grid(n, V->p, sms)
                    : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, sms);
@@ -89,10 +90,10 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   if (max_grid < 2) return STMF_ENOMEM;  // (n + 1) * r too large for the scratch
   if (size_t(grid) > max_grid - 1) grid = int(max_grid - 1);
 
-  double* scratch = nullptr;
-  stmf_status st = scratch_for_current_device(&scratch);
-  if (st != STMF_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  stmf_status st = scratch_for_current_device(s, &scratch);
+  if (st != STMF_OK) return st;
   int32_t* status_word = status;
   if (!status_word) {
     status_word = reinterpret_cast<int32_t*>(scratch + kScratchDoubles);
@@ -134,6 +135,7 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   mp.r = (int)r;
   mp.d = d;
   mp.status = status_word;
+  mp.poison = 1;  // an error recorded during this call (or left in a caller's word) gives NaN
   e = stmf::model_terms_launch(mp, s);
   return e == cudaSuccess ? STMF_OK : STMF_ECUDA;
 }

@@ -73,6 +73,18 @@ __global__ void __launch_bounds__(RE * RY) reduce_kernel(const ModelParams prm, 
 
 __global__ void __launch_bounds__(RT) finalize_kernel(const ModelParams prm) {
   if (prm.skip && *prm.skip) return;
+  if (prm.poison && *(volatile int32_t*)prm.status != 0) {
+    // an earlier step of this evaluation reported an error (e.g. a pass whose bounded wait ran
+    // out left its block partials unwritten): the outputs must not look like a valid result
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    const int e = blockIdx.x * RT + threadIdx.x;
+    if (e < prm.n * prm.r) prm.G_A[e] = qnan;
+    if (blockIdx.x == 0) {
+      for (int j = threadIdx.x; j < prm.r; j += RT) prm.g_lambda[j] = qnan;
+      if (threadIdx.x == 0) *prm.f = qnan;
+    }
+    return;
+  }
   __shared__ double Cs[64 * 64];
   __shared__ double lam[64];
   __shared__ double us[64];

@@ -277,6 +277,7 @@ void stmf_server::run() {
       int busy = 0;
       for (auto& s : slots) busy += s.req != nullptr;
       stats.active_fits = busy;
+      if (busy > stats.peak_active_fits) stats.peak_active_fits = busy;
       if (notify) cv.notify_all();
     }
     if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));

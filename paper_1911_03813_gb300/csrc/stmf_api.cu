@@ -14,8 +14,8 @@
 
 namespace {
 
-constexpr size_t kMaxSmem = 232448;  // dynamic shared memory per block on sm_103
-constexpr int64_t kMaxN = 512;       // features per sample
+using stmf::kMaxN;
+using stmf::kMaxSmem;
 
 stmf_status fail(stmf_ctx* c, stmf_status st, const std::string& msg) {
   if (c) c->last_error = msg;
@@ -35,18 +35,8 @@ stmf_status check_device(stmf_ctx* c) {
 }
 
 stmf_status check_samples(stmf_ctx* c, const stmf_samples* V) {
-  if (!V) return fail(c, STMF_EINVAL, "V is NULL");
-  if (!V->data) return fail(c, STMF_EINVAL, "V->data is NULL");
-  const int eb = stmf::elem_bytes(V->dtype);
-  if (eb == 0) return fail(c, STMF_EINVAL, "V->dtype is not a stmf_dtype");
-  if (V->n < 1 || V->n > kMaxN) return fail(c, STMF_EINVAL, "V->n must be in [1, 512]");
-  if (V->p < 1) return fail(c, STMF_EINVAL, "V->p must be >= 1");
-  if (V->p > (int64_t(1) << 40)) return fail(c, STMF_EINVAL, "V->p is too large");
-  if (V->ld < V->n) return fail(c, STMF_EINVAL, "V->ld must be >= V->n");
-  if ((V->ld * eb) % 16 != 0) return fail(c, STMF_EINVAL, "V->ld * element size must be a multiple of 16 bytes");
-  if ((reinterpret_cast<uintptr_t>(V->data) & 15) != 0) return fail(c, STMF_EINVAL, "V->data must be 16-byte aligned");
-  if (V->dtype == STMF_E4M3 && !V->scale) return fail(c, STMF_EINVAL, "E4M3 samples need V->scale");
-  if (V->dtype != STMF_E4M3 && V->scale) return fail(c, STMF_EINVAL, "V->scale is only used with E4M3 samples");
+  const char* why = stmf::samples_problem(V);
+  if (why) return fail(c, STMF_EINVAL, why);
   return check_device(c);
 }
 
@@ -106,6 +96,22 @@ cudaError_t stmf::smem_limit(const void* kernel, int bytes) {
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) done[key] = bytes;
   return e;
+}
+
+const char* stmf::samples_problem(const stmf_samples* V) {
+  if (!V) return "V is NULL";
+  if (!V->data) return "V->data is NULL";
+  const int eb = stmf::elem_bytes(V->dtype);
+  if (eb == 0) return "V->dtype is not a stmf_dtype";
+  if (V->n < 1 || V->n > kMaxN) return "V->n must be in [1, 512]";
+  if (V->p < 1) return "V->p must be >= 1";
+  if (V->p > stmf::kMaxP) return "V->p is too large";
+  if (V->ld < V->n) return "V->ld must be >= V->n";
+  if ((V->ld * eb) % 16 != 0) return "V->ld * element size must be a multiple of 16 bytes";
+  if ((reinterpret_cast<uintptr_t>(V->data) & 15) != 0) return "V->data must be 16-byte aligned";
+  if (V->dtype == STMF_E4M3 && !V->scale) return "E4M3 samples need V->scale";
+  if (V->dtype != STMF_E4M3 && V->scale) return "V->scale is only used with E4M3 samples";
+  return nullptr;
 }
 
 stmf_status stmf::set_error(stmf_ctx* c, stmf_status st, const std::string& msg) {

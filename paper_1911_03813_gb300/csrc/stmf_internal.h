@@ -11,6 +11,14 @@
 
 namespace stmf {
 
+constexpr size_t kMaxSmem = 232448;  // dynamic shared memory per block on sm_103
+constexpr int64_t kMaxN = 512;       // features per sample
+constexpr int64_t kMaxP = int64_t(1) << 40;  // samples per call
+
+// Checks of a sample descriptor that need no context (pointers, sizes, alignment, dtype and
+// scale): nullptr when V is acceptable, else a description of the first problem.
+const char* samples_problem(const stmf_samples* V);
+
 // Launch parameters of the fused pass over V (Alg. 2: Y, and the sums behind w).
 struct FgParams {
   const void* V;        // sample-major storage, p rows of ld elements
@@ -46,6 +54,7 @@ struct ModelParams {
   int32_t* status;
   const int32_t* skip;     // as in FgParams
   int accumulate;          // reduce_partials: yw += sum (instead of yw = sum)
+  int poison;              // finalize: write NaN to f, g_lambda and G_A when *status != 0
 };
 
 struct GramParams {

@@ -183,13 +183,9 @@ def as_samples(V, n=None, scale=None):
     return desc, (V, scale)
 
 
-def fg(V, nu, d, lam, A, alpha=None, out=None, stream=None, ctx=None):
-    """f, g_lambda, G_A of Alg. 2 (stmf_fg). lam: (r,) float64 CUDA; A: (n, r) float64 CUDA in
-    column-major order (pass A as a Fortran-ordered view, e.g. At.T for At of shape (r, n)).
-    nu: (p,) float64 CUDA or None (1/p). alpha: (1,) float64 CUDA or None (0).
-    Returns device tensors (f (1,), g_lambda (r,), G_A as an (n, r) column-major view)."""
-    ctx = ctx or default_context()
-    desc, keep = as_samples(V)
+def _check_model_args(desc, nu, lam, A, alpha, out):
+    """Validate the model arguments shared by fg() and fg_noalloc() and return the output
+    tensors (f (1,), g_lambda (r,), G_A (n, r) column-major), allocating them unless given."""
     n, p = desc.n, desc.p
     r = lam.shape[0]
     _check_f64(lam, (r,), "lambda")
@@ -207,6 +203,23 @@ def fg(V, nu, d, lam, A, alpha=None, out=None, stream=None, ctx=None):
         GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
     else:
         f, gl, GA = out
+        _check_f64(f, (1,), "f")
+        _check_f64(gl, (r,), "g_lambda")
+        if (GA.dtype != torch.float64 or not GA.is_cuda or tuple(GA.shape) != (n, r)
+                or not ((GA.stride(0) == 1 or n == 1) and (GA.stride(1) == n or r == 1))):
+            raise ValueError("G_A must be an (n, r) column-major CUDA float64 tensor")
+    return f, gl, GA
+
+
+def fg(V, nu, d, lam, A, alpha=None, out=None, stream=None, ctx=None):
+    """f, g_lambda, G_A of Alg. 2 (stmf_fg). lam: (r,) float64 CUDA; A: (n, r) float64 CUDA in
+    column-major order (pass A as a Fortran-ordered view, e.g. At.T for At of shape (r, n)).
+    nu: (p,) float64 CUDA or None (1/p). alpha: (1,) float64 CUDA or None (0).
+    Returns device tensors (f (1,), g_lambda (r,), G_A as an (n, r) column-major view)."""
+    ctx = ctx or default_context()
+    desc, keep = as_samples(V)
+    r = lam.shape[0]
+    f, gl, GA = _check_model_args(desc, nu, lam, A, alpha, out)
     st = lib().stmf_fg(ctx.handle, ctypes.byref(desc), _ptr(nu), int(d), int(r), _ptr(lam),
                        _ptr(A), _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _stream(stream))
     ctx.check(st, "stmf_fg")
@@ -271,18 +284,15 @@ def fg_noalloc(V, nu, d, lam, A, alpha=None, out=None, status=None, stream=None)
     memory; the library uses a fixed scratch array in its device globals instead of a context
     workspace. Calls on one device share that array, so calls that overlap on the GPU race.
     Output tensors (f, g_lambda, G_A) may be passed in `out` so that the call itself allocates
-    nothing; `status` is an optional (1,) int32 CUDA tensor that receives device-side errors."""
+    nothing; `status` is an optional (1,) int32 CUDA tensor that receives device-side errors
+    (the call does not clear it). Whenever a device-side error is recorded (in `status` or, when
+    it is None, in a word of the scratch), f, g_lambda and G_A come back as NaN."""
     desc, keep = as_samples(V)
-    n, r = desc.n, lam.shape[0]
-    _check_f64(lam, (r,), "lambda")
-    if A.dtype != torch.float64 or not A.is_cuda or tuple(A.shape) != (n, r):
-        raise ValueError("A must be an (n, r) CUDA float64 tensor")
-    if out is None:
-        f = torch.empty(1, dtype=torch.float64, device=lam.device)
-        gl = torch.empty(r, dtype=torch.float64, device=lam.device)
-        GA = torch.empty((r, n), dtype=torch.float64, device=lam.device).T
-    else:
-        f, gl, GA = out
+    r = lam.shape[0]
+    f, gl, GA = _check_model_args(desc, nu, lam, A, alpha, out)
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda
+                               or tuple(status.shape) != (1,)):
+        raise ValueError("status must be a (1,) int32 CUDA tensor")
     st = lib().stmf_fg_noalloc(ctypes.byref(desc), _ptr(nu), int(d), int(r), _ptr(lam), _ptr(A),
                                _ptr(alpha), _ptr(f), _ptr(gl), _ptr(GA), _ptr(status),
                                _stream(stream))
@@ -382,7 +392,8 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_int64), ("active_fits", ctypes.c_int32),
                 ("queued", ctypes.c_int32), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes_in_use", ctypes.c_size_t), ("slot_bytes", ctypes.c_size_t),
-                ("now", ctypes.c_double)]
+                ("now", ctypes.c_double), ("peak_active_fits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def _declare_server(L):

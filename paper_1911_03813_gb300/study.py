@@ -18,16 +18,37 @@ from . import inputs, stmf
 
 def score(A_true, A):
     """eq. Score: the best one-to-one matching between the computed and the true component
-    directions (unit-normalised columns), averaged |cosine| over the smaller set. The matching is
-    an assignment problem (solved with SciPy's linear_sum_assignment)."""
-    from scipy.optimize import linear_sum_assignment
+    directions (unit-normalised columns), averaged |cosine| over the smaller set.
+
+    The matching is found exactly by dynamic programming over subsets: with k columns on the
+    smaller side and m on the larger (k <= m), best[S] is the largest sum of |cosines| that
+    matches the first |S| small-side columns to the large-side set S, and
+    best[S | {c}] = max(best[S] + C[|S|, c]) over c not in S. That is O(m 2^m) work, which suits
+    the ranks of the study (m <= 16)."""
     U = np.asarray(A_true, dtype=np.float64)
     W = np.asarray(A, dtype=np.float64)
     U = U / np.linalg.norm(U, axis=0, keepdims=True)
     W = W / np.linalg.norm(W, axis=0, keepdims=True)
     C = np.abs(U.T @ W)
-    rows, cols = linear_sum_assignment(C, maximize=True)
-    return float(C[rows, cols].sum() / min(C.shape))
+    if C.shape[0] > C.shape[1]:
+        C = C.T                       # rows: the smaller set
+    k, m = C.shape
+    if m > 20:
+        raise ValueError("score: at most 20 components per side")
+    best = np.full(1 << m, -np.inf)
+    best[0] = 0.0
+    popcount = np.array([bin(S).count("1") for S in range(1 << m)])
+    for S in range(1 << m):
+        i = popcount[S]
+        if i >= k or best[S] == -np.inf:
+            continue
+        for c in range(m):
+            if not S & (1 << c):
+                T = S | (1 << c)
+                v = best[S] + C[i, c]
+                if v > best[T]:
+                    best[T] = v
+    return float(best[popcount == k].max() / k)
 
 
 def scenario(server, d, r, sigma, n=500, starts=10, dtype="f32", pgtol=1e-4, max_evals=20000,

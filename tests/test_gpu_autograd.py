@@ -3,7 +3,7 @@
 Differentiation workload: n = 64, d = 3, r = 8, p = 1e6 FP32 Gaussian-mixture samples. The
 objective is wrapped in an outer loss L = f(lambda, A) + sum_j (||a_j|| - 1)^2; its autograd
 gradient is checked against central finite differences (step 1e-3) along 200 random unit
-directions and against the oracle's gradient; backward is timed against forward.
+directions and against the oracle's gradient; backward is checked to make no pass over V.
 """
 
 import numpy as np
@@ -76,26 +76,39 @@ def test_autograd_matches_oracle_and_finite_differences(setup):
     print("worst FD error / band: %.3f" % worst)
 
 
-def test_backward_is_cheap_against_forward(setup):
-    ag, st, d = setup["autograd"], setup["st"], setup["d"]
+def test_backward_makes_no_pass_over_samples(setup):
+    """Backward is the chain rule applied to the gradient the forward pass already produced
+    (eqs. gradl and gradb come out of Alg. 2 with f): it launches no pass over V and returns
+    exactly grad_out times that gradient. The pass count comes from the library's own event
+    record, so host scheduling noise cannot change the outcome; the time of each direction is
+    printed for information (bench.py reports it)."""
+    ag, st, d, stmf = setup["autograd"], setup["st"], setup["d"], setup["stmf"]
     lam = torch.tensor(setup["lam0"], device="cuda", requires_grad=True)
     A = torch.tensor(setup["A0"], device="cuda", requires_grad=True)
-    for _ in range(3):
+    stmf.profile_enable(True)
+    try:
+        stmf.profile_read()                      # clear the record
         f = ag.objective(lam, A, st, None, d)
-        f.backward()
+        fwd_ms, fwd_passes = stmf.profile_read()
+        f.backward(torch.tensor(2.5, dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        _, bwd_passes = stmf.profile_read()
+    finally:
+        stmf.profile_enable(False)
+    assert fwd_passes == 1
+    assert bwd_passes == 0
+    # the same evaluation outside autograd (fixed-order reductions: bit-identical)
+    A_c = A.detach().t().contiguous().t()
+    _, gl, GA = stmf.fg(st, None, d, lam.detach(), A_c)
+    torch.cuda.synchronize()
+    assert torch.equal(lam.grad, 2.5 * gl)
+    assert torch.equal(A.grad, 2.5 * GA)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    fwd = bwd = 0.0
-    for _ in range(20):
-        lam.grad = None
-        A.grad = None
-        torch.cuda.synchronize()
-        e[0].record()
-        f = ag.objective(lam, A, st, None, d)
-        e[1].record()
-        f.backward()
-        e[2].record()
-        torch.cuda.synchronize()
-        fwd += e[0].elapsed_time(e[1])
-        bwd += e[1].elapsed_time(e[2])
-    print("forward %.3f ms, backward %.3f ms per call" % (fwd / 20, bwd / 20))
-    assert bwd < 0.25 * fwd
+    e[0].record()
+    f = ag.objective(lam, A, st, None, d)
+    e[1].record()
+    f.backward()
+    e[2].record()
+    torch.cuda.synchronize()
+    print("forward %.3f ms (pass %.3f ms), backward %.3f ms"
+          % (e[0].elapsed_time(e[1]), fwd_ms, e[1].elapsed_time(e[2])))

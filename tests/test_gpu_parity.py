@@ -9,6 +9,8 @@ values the GPU reads (BF16 codes widened, E4M3 codes times their scales). Tolera
                           products carry ~2^-17 relative error before FP32 accumulation)
 """
 
+import json
+
 import numpy as np
 import pytest
 
@@ -57,12 +59,28 @@ def run_fg(stmf, st, nu, lam, A, d, alpha=None):
     return f.item(), gl.cpu().numpy(), GA.cpu().numpy()
 
 
-def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0):
+def elementwise(a, b, c):
+    """max_i |a_i - b_i| / (|b_i| + c max_k |b_k|): every entry relative to itself, with a floor
+    of c times the largest entry for entries that are small because their terms cancel."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.max(np.abs(a - b) / (np.abs(b) + c * np.max(np.abs(b)) + 1e-300)))
+
+
+def report(tag, **vals):
+    print("PARITY " + json.dumps(dict(tag=tag, **vals)))
+
+
+def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0, tag=""):
     Vd = decoded(st)
     f_ref, gl_ref, GA_ref, parts = oracle.fg_implicit(nu, Vd.T, lam, A, d, alpha=alpha,
                                                       return_parts=True)
     f, gl, GA = run_fg(stmf, st, nu, lam, A, d, alpha=alpha)
     S = abs(alpha) + abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
+    report(tag or st["dtype"], n=int(A.shape[0]), r=int(A.shape[1]), d=d, f=abs(f - f_ref) / S,
+           gl_norm=rel(gl, gl_ref), GA_norm=rel(GA, GA_ref),
+           gl_el={c: elementwise(gl, gl_ref, c) for c in (0.01, 0.1, 1.0)},
+           GA_el={c: elementwise(GA, GA_ref, c) for c in (0.01, 0.1, 1.0)})
     assert abs(f - f_ref) <= tol * S, (f, f_ref, S)
     assert rel(gl, gl_ref) <= tol, rel(gl, gl_ref)
     assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
@@ -81,6 +99,9 @@ SHAPES = [
     (256, 70000, 16, 4),
     (128, 3000, 64, 2),   # r at its maximum, the matrix case
     (256, 300, 33, 5),
+    (129, 3001, 16, 3),   # tensor-core passes between 128 and 256 features: a second M block
+    (160, 5000, 12, 4),   #   of MMA2 that is partly padding, and K steps past one 128-feature
+    (192, 7001, 16, 3),   #   half of the tile
 ]
 
 

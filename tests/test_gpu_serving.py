@@ -101,19 +101,12 @@ def test_admission_by_memory_and_overlap(stmf):
     one = p * n * 2 + 2048      # samples copy + start vector (rounded up)
     with _server_with_room(stmf, 3 * one) as srv:
         tickets = [srv.submit(V, d, x0, **opts) for V, x0, _ in reqs]
-        seen_active = 0
-        while True:
-            s = srv.stats()
-            seen_active = max(seen_active, s["active_fits"])
-            assert s["bytes_in_use"] <= 3 * one + 4096
-            if s["completed"] == len(reqs):
-                break
-            time.sleep(0.002)
         results = [srv.poll(t) for t in tickets]
         s = srv.stats()
     assert all(r_["state"] == 0 for r_ in results)
-    assert s["peak_bytes_in_use"] <= 3 * one + 4096
-    assert seen_active >= 2          # fits ran side by side
+    assert s["peak_bytes_in_use"] <= 3 * one + 4096   # the budget admitted at most 3 at once
+    assert s["peak_active_fits"] >= 2                  # fits ran side by side
+    assert s["peak_active_fits"] <= 3
     assert max(r_["t_admit"] for r_ in results) > min(r_["t_done"] for r_ in results)  # queued
 
 

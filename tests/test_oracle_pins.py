@@ -370,6 +370,74 @@ def test_adam_first_step_and_schedule():
     assert out["epochs"] >= 1
 
 
+class _ScriptedSampledObjective:
+    """Stand-in for the oracle's fg_sampled with everything known in advance. The estimation
+    rows are marked by the index -1: the k-th estimate returns script[k] (the last entry once the
+    script runs out, so a method that fails to stop runs on and fails the checks). A step row [t] returns
+    the gradient +1 in every coordinate, or -1 for t in `reverse`. With a constant gradient g,
+    every bias-corrected Adam step moves each coordinate by exactly -lr g / (|g| + eps), whatever
+    the step count (m_t / (1 - beta1^t) = g and v_t / (1 - beta2^t) = g^2); a history that mixes
+    -1 and +1 does not give that step, so a moment that was not rolled back shows."""
+
+    def __init__(self, script, reverse=()):
+        self.script = list(script)
+        self.reverse = set(reverse)
+        self.estimates = 0
+        self.steps = []
+
+    def __call__(self, V, idx, lam, A, d, alpha=0.0):
+        idx = np.asarray(idx)
+        r = len(lam)
+        if idx[0] == -1:
+            f = self.script[min(self.estimates, len(self.script) - 1)]
+            self.estimates += 1
+            return f, np.zeros(r), np.zeros(np.shape(A))
+        t = int(idx[0])
+        self.steps.append(t)
+        sgn = -1.0 if t in self.reverse else 1.0
+        return 0.0, np.full(r, sgn), np.full(np.shape(A), sgn)
+
+
+@pytest.mark.parametrize("case", ["drop_then_stop", "drop_at_first_epoch"])
+def test_adam_schedule_pinned(monkeypatch, case):
+    """Sec. 5's schedule on scripted estimates: the learning rate drops from 1e-2 to 1e-3 exactly
+    at the first non-decrease of the epoch estimate, the iterate, both Adam moments and the step
+    count return to the end of the prior epoch, and the second non-decrease stops the method with
+    the prior epoch's iterate and estimate. The step rows keep advancing through a rollback (each
+    iteration draws fresh samples)."""
+    n, r, d, epoch = 3, 2, 3, 100
+    lam0 = np.array([0.5, 0.25])
+    A0 = np.arange(n * r, dtype=np.float64).reshape(n, r) / 7.0
+    x0 = np.concatenate([lam0, A0.reshape(-1, order="F")])
+    step0 = 1e-2 / (1.0 + 1e-8)
+    step1 = 1e-3 / (1.0 + 1e-8)
+    if case == "drop_then_stop":
+        # estimates: start 10; epochs 1, 2 decrease; epoch 3 does not (its gradient is reversed,
+        # and it is rolled back); epoch 4 decreases at the lower rate; epoch 5 does not: stop
+        stub = _ScriptedSampledObjective([10.0, 9.0, 8.0, 8.5, 7.0, 7.5],
+                                         reverse=range(2 * epoch, 3 * epoch))
+        x_expected = x0 - 2 * epoch * step0 - epoch * step1
+        f_expected, epochs_expected = 7.0, 5
+        trace_expected = [10.0, 9.0, 8.0, 8.5, 7.0, 7.5]
+    else:
+        # the first epoch's estimate does not decrease: back to the start (zero moments, t = 0)
+        # at the lower rate; epoch 2 decreases; epoch 3 does not: stop with epoch 2's iterate
+        stub = _ScriptedSampledObjective([5.0, 5.0, 4.0, 4.0], reverse=range(0, epoch))
+        x_expected = x0 - epoch * step1
+        f_expected, epochs_expected = 4.0, 3
+        trace_expected = [5.0, 5.0, 4.0, 4.0]
+    monkeypatch.setattr(stochastic, "fg_sampled", stub)
+    sample_idx = np.arange(10 * epoch).reshape(-1, 1)
+    est_idx = np.array([-1])
+    out = stochastic.adam(None, lam0, A0, d, sample_idx, est_idx, epoch=epoch)
+    x = np.concatenate([out["lam"], out["A"].reshape(-1, order="F")])
+    np.testing.assert_allclose(x, x_expected, rtol=1e-12, atol=1e-14)
+    assert out["f_est"] == f_expected
+    assert out["epochs"] == epochs_expected
+    assert out["trace"] == trace_expected
+    assert stub.steps == list(range(epochs_expected * epoch))
+
+
 def test_rrf_start_in_range_of_samples():
     g = np.random.default_rng(5)
     V = g.standard_normal((10, 4)) @ g.standard_normal((4, 50))     # rank-4 sample matrix

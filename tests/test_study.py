@@ -8,18 +8,30 @@ from oracle import score as oscore
 from paper_1911_03813_gb300 import inputs, study
 
 
-@pytest.mark.parametrize("r,r_hat", [(3, 3), (5, 3), (3, 5), (10, 8)])
+@pytest.mark.parametrize("r,r_hat", [(3, 3), (5, 3), (3, 5), (7, 6), (6, 7), (1, 4), (4, 1),
+                                     (10, 8), (12, 12)])
 def test_score_matches_oracle(r, r_hat):
+    """The study's own assignment search (dynamic programming over subsets) against the oracle's
+    enumeration of every one-to-one map (up to 7 components), and against the oracle's Hungarian
+    form above that."""
     g = inputs.rng(100 * r + r_hat)
     A_true = g.standard_normal((40, r))
     A = A_true[:, g.permutation(r)[: min(r, r_hat)]] * g.choice([-2.0, 3.0], min(r, r_hat))
     if r_hat > r:
         A = np.concatenate([A, g.standard_normal((40, r_hat - r))], axis=1)
     A = A + 0.1 * g.standard_normal(A.shape)
-    assert study.score(A_true, A) == pytest.approx(oscore.score(A_true, A), abs=1e-14)
     if max(r, r_hat) <= 7:
         assert study.score(A_true, A) == pytest.approx(oscore.score_bruteforce(A_true, A),
                                                        abs=1e-14)
+    else:
+        assert study.score(A_true, A) == pytest.approx(oscore.score(A_true, A), abs=1e-14)
+
+
+def test_score_is_one_for_a_permuted_rescaled_copy():
+    g = inputs.rng(5)
+    A_true = g.standard_normal((20, 6))
+    A = A_true[:, [4, 2, 0, 5, 1, 3]] * np.array([-1.0, 2.0, 0.5, -3.0, 1.0, 7.0])
+    assert study.score(A_true, A) == pytest.approx(1.0, abs=1e-14)
 
 
 @pytest.mark.gpu
