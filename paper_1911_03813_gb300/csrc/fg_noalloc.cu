@@ -77,12 +77,9 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   if (!(major == 10 && minor == 3)) return STMF_EUNSUPPORTED;
 
   const int n = (int)V->n;
-  const bool tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
-  const bool f32 = !tc && stmf::fg_f32_supported(V->dtype, n, (int)r);
-  if (!tc && !f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > stmf::kMaxSmem) return STMF_EINVAL;
-  int grid = tc    ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, sms)
-             : f32 ? stmf::fg_f32_grid(n, V->p, sms)
-                   : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, sms);
+  stmf::PassPlan pass{};
+  if (!stmf::plan_pass(V->dtype, n, (int)r, V->p, sms, false, &pass)) return STMF_EINVAL;
+  int grid = pass.grid;
   // the partials of `grid` blocks plus the reduced (w, Y) must fit the fixed scratch; the pass is
   // persistent, so fewer blocks only means fewer tiles in flight
   const size_t L = size_t(r) + size_t(n) * size_t(r);
@@ -115,9 +112,8 @@ extern "C" stmf_status stmf_fg_noalloc(const stmf_samples* V, const double* nu, 
   prm.r_pad = (int)((r + 3) / 4 * 4);
   prm.flush_tiles = 16;
   prm.status = status_word;
-  cudaError_t e = tc    ? stmf::fg_tc_launch(V->dtype, prm, grid, s)
-                  : f32 ? stmf::fg_f32_launch(prm, grid, s)
-                        : stmf::fg_simt_launch(V->dtype, prm, grid, s);
+  pass.grid = grid;
+  cudaError_t e = stmf::launch_pass(pass, V->dtype, prm, s);
   if (e != cudaSuccess) return STMF_ECUDA;
 
   stmf::ModelParams mp{};

@@ -1,0 +1,672 @@
+// Fused pass over FP32 samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM).
+//
+// Computes the same per-CTA partial sums of Alg. 2 as the BF16 pass (Lemma 3.3, eq. Y; Lemma 3.5):
+//     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
+// reading every FP32 sample from HBM exactly once.
+//
+// Each FP32 value x is split in shared memory into two BF16 terms, b1 = bf16(x) and
+// b2 = bf16(x - b1), which carry x to 2^-18 relative (x - b1 is exact in FP32; b2 keeps its
+// leading 8 bits). The pair occupies the 4 bytes x came in, so the split is done in place and
+// the pass becomes the BF16 pass over 2n "features": z = [b1 b2] [A; A] and the two halves of
+// V^T W are summed at the end. Tiles of 128 samples arrive as sub-stages of 64 features
+// (32 KB: two TMA boxes, regions, of 32 FP32 features). Per sub-stage h of a tile:
+//   convert  region g (features 32g .. 32g + 31 of the sub-stage) becomes, row by row,
+//            [b1 of its 32 features | b2 of its 32 features] (BF16, 128-byte swizzle)
+//   MMA1     Z_b1 += b1 [A1, A2, A3](features 64h..)       M = 128 samples, N = 3 RP (16-padded)
+//            Z_b2 += b2 [A1, A2]                            N = 2 RP
+//   MMA2     Y_h += [b1 ; b2]^T [W_hi, W_lo]                M = 128 (b1 rows, then b2 rows)
+// MMA2's block h reads only sub-stage h and releases it when done, so a tile of n <= 256
+// features needs at most four 32 KB sub-stages at a time and the ring of six keeps the next tile
+// streaming in. A (FP64) is split once per CTA into three BF16 terms A1 + A2 + A3 (2^-25
+// relative): the split of A is the same perturbation for every sample, so unlike the rounding of
+// W and V it does not average out over samples, and a two-term split (2^-17) would show in the
+// small entries of G_A. W is split per tile into BF16 hi/lo, as in the BF16 pass. The tensor
+// cores' FP32 accumulation truncates, so every addition into an accumulator biases |z| low by
+// up to an ulp of the running sum: the b1 products go to two accumulators (even and odd
+// sub-stages, as the BF16 pass splits K) and the b2 products, 2^-8 of the size, to a third, so
+// no accumulator takes more additions than in the BF16 pass.
+//
+// So each K step of 16 of MMA1 is either all b1 or all b2, and the rows of MMA2 block h are
+// [b1 f0-31; b2 f0-31; b1 f32-63; b2 f32-63] of sub-stage h's features.
+//
+// Warp roles (864 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
+// warp 2 = MMA2 issuer, warps 3-18 = epilogue (four warpgroups that split the components;
+// thread = TMEM lane = sample of the tile, or row of an MMA2 block), warps 19-26 = converters
+// (thread = one row of one region, so the in-place rewrite never crosses threads; eight warps,
+// two per scheduler, keep the conversion's dependent arithmetic off the critical path). Every
+// wait is bounded: a wait that runs out sets STMF_ETIMEOUT in the status word and all roles
+// wind down, wait for their own copies and MMAs, and free TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "stmf_internal.h"
+#include "tc_common.cuh"
+
+namespace stmf {
+namespace {
+
+constexpr int TM = 128;                  // samples per tile
+constexpr int REG_BYTES = TM * 128;      // one region: 128 rows of 128 bytes (16 KB)
+constexpr int SUB_BYTES = 2 * REG_BYTES; // one sub-stage: 64 FP32 features of 128 samples
+constexpr int MAX_SUB = 4;               // n <= 256
+constexpr int EG = 4;                    // epilogue warpgroups
+constexpr int NEPI = 128 * EG;
+constexpr int NCONV = 8;                 // converter warps: 128 rows x 2 regions
+constexpr int CONV0 = 96 + NEPI;         // first converter thread
+constexpr int NTHREADS = CONV0 + 32 * NCONV;
+constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
+
+struct Tc32Extra {
+  int nsub;        // sub-stages per tile: ceil(n / 64)
+  int zbufs;       // Z buffers in TMEM: 2 where they fit beside Y, else 1
+  int ring;        // sub-stage slots in shared memory
+  int wbufs;       // W buffers: 2, or 1 where a second one would cost a ring slot
+  int flush;       // tiles between folds of Y into compensated FP32 registers
+  int tmem_cols;
+  int smem_bytes;
+};
+
+// MMA1 columns (rows of the A split, columns of Z in TMEM) are term-major: column of
+// (component j, term k) = k RP + j; rows past 3 RP are zero. The b2 products use the first 2 RP
+// rows (A1 and A2 only: b2 A3 is below 2^-24 of z). A warpgroup reads its CPG components of
+// each term with one load of CPG columns at a multiple of CPG.
+// TMEM: each Z buffer (ZBS columns) holds the b1 accumulators at columns 0 and ZS and the b2
+// accumulator at 2 ZS; Y follows the Z buffers, 2 buffers x nsub blocks of N2 columns. Two Z
+// buffers (MMA1 of the next tile runs while the epilogue reads this one) fit beside Y for
+// n <= 128; above that there is one. Every MMA's columns start at a multiple of 2 RP and every
+// load at a multiple of its width.
+template <int RP>
+struct Cfg32 {
+  static constexpr int CPG = RP / EG;
+  static constexpr int N1 = (3 * RP + 15) / 16 * 16;  // MMA1 N for b1: three terms
+  static constexpr int NB2 = 2 * RP;                  // MMA1 N for b2: two terms
+  static constexpr int N2 = 2 * RP;                   // MMA2 N: W hi and lo
+  static constexpr int ZS = (N1 + 2 * RP - 1) / (2 * RP) * (2 * RP);  // b1 accumulator stride
+  static constexpr int ZBS = 2 * ZS + NB2;            // one Z buffer: 160 or 80 columns
+  static constexpr int W_REG = N2 * 128;              // one 64-sample region of W
+  static constexpr int A_REG = N1 * 128;              // one 64-feature region of the A split
+};
+
+// TMEM columns of a plan: Z buffers, then 2 x nsub Y blocks.
+__host__ __device__ constexpr int tmem_need(int zbs, int zbufs, int nsub, int n2) {
+  return zbs * zbufs + 2 * nsub * n2;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ float ipow_f(float z, int e) {
+  float t = z;
+  for (int k = 1; k < e; ++k) t *= z;
+  return t;
+}
+
+template <int C>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
+  if constexpr (C == 8) {
+    tc::tmem_ld8(taddr, v);
+  } else if constexpr (C == 4) {
+    tc::tmem_ld4(taddr, v);
+  } else {
+    static_assert(C == 2, "2, 4 or 8 columns per load");
+    tc::tmem_ld2(taddr, v);
+  }
+}
+
+// z of one warpgroup's CPG components from a Z buffer at `zaddr`: the b2 accumulator's two
+// terms, the second b1 accumulator's three (when there is more than one sub-stage) and the
+// first's three, each accumulator's terms summed smallest first, in FP32 rounded to nearest.
+template <int CPG, int RP, int ZS>
+__device__ __forceinline__ void tmem_z(uint32_t zaddr, bool two_b1, float (&z)[CPG]) {
+  float v[8][CPG];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(k * RP), v[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (two_b1) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[3 + k]);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[6 + k]);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int c = 0; c < CPG; ++c) {
+    float t = v[7][c] + v[6][c];
+    if (two_b1) t += (v[5][c] + v[4][c]) + v[3][c];
+    z[c] = t + ((v[2][c] + v[1][c]) + v[0][c]);
+  }
+}
+
+// Eight FP32 values -> their BF16 leading terms (b1) and BF16 remainders (b2), packed in pairs.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+    const uint32_t u = *reinterpret_cast<const uint32_t*>(&b);
+    const float r0 = x[2 * k] - __uint_as_float(u << 16);          // exact
+    const float r1 = x[2 * k + 1] - __uint_as_float(u & 0xFFFF0000u);
+    const __nv_bfloat162 c = __floats2bfloat162_rn(r0, r1);
+    h[k] = u;
+    l[k] = *reinterpret_cast<const uint32_t*>(&c);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void epi_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NEPI) : "memory");
+}
+
+// NS: sub-stages per tile the epilogue keeps Y sums for (1, 2 or 4; at least ex.nsub).
+template <int RP, int NS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    fg_tc32_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const Tc32Extra ex) {
+  using C = Cfg32<RP>;
+  constexpr int N1 = C::N1;
+  constexpr int N2 = C::N2;
+  constexpr int CPG = C::CPG;
+  constexpr int ZS = C::ZS;
+  const int ZBUF = ex.zbufs;
+  const uint32_t YB0 = uint32_t(C::ZBS * ZBUF);  // first Y column
+  if (prm.skip && *prm.skip) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw_addr = tc::smem_addr(smem_raw);
+  unsigned char* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+
+  const int R = ex.ring, nsub = ex.nsub, WB = ex.wbufs;
+  const int n = prm.n, r = prm.r, d = prm.d;
+  unsigned char* sV = base;                              // ring of R sub-stages
+  unsigned char* sW = sV + size_t(R) * SUB_BYTES;        // WB buffers x 2 regions
+  unsigned char* sA = sW + size_t(WB) * 2 * C::W_REG;    // nsub regions
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nsub) * C::A_REG);
+  uint64_t* full = bars;            // [R] TMA landed
+  uint64_t* conv = bars + R;        // [R] split into BF16 terms
+  uint64_t* empty = bars + 2 * R;   // [R] MMA2 done with the sub-stage
+  uint64_t* zfull = bars + 3 * R;  // [ZBUF]
+  uint64_t* zempty = zfull + 2;
+  uint64_t* wfull = zempty + 2;
+  uint64_t* wempty = wfull + 2;
+  uint64_t* yfull = wempty + 2;
+  uint64_t* yempty = yfull + 2;
+  uint64_t* mma_done = yempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  double* wred = reinterpret_cast<double*>(mma_done + 3);  // 4 x RP
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], NCONV);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&zfull[b], 1);
+      tc::mbar_init(&zempty[b], NEPI / 32);
+      tc::mbar_init(&wfull[b], NEPI / 32);
+      tc::mbar_init(&wempty[b], 1);
+      tc::mbar_init(&yfull[b], 1);
+      tc::mbar_init(&yempty[b], NEPI / 32);
+    }
+    tc::mbar_init(&mma_done[0], 1);
+    tc::mbar_init(&mma_done[1], 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
+
+  // A split: row k RP + j holds term k of a_j, with A1 = BF16(a), A2 = BF16(a - A1),
+  // A3 = BF16(a - A1 - A2) (rows past 3 RP are zero); the same region h serves the b1 and the b2
+  // half of sub-stage h
+  {
+    const int kext = nsub * 64;
+    for (int e = tid; e < N1 * kext; e += NTHREADS) {
+      const int row = e / kext, k = e - row * kext;
+      const int term = row / RP, j = row % RP;
+      const double a = (term < 3 && j < r && k < n) ? prm.A[k + size_t(n) * j] : 0.0;
+      const double a1 = (double)__bfloat162float(__double2bfloat16(a));
+      const double a2 = (double)__bfloat162float(__double2bfloat16(a - a1));
+      const double v = term == 0 ? a1 : term == 1 ? a2 : a - a1 - a2;
+      *reinterpret_cast<__nv_bfloat16*>(sA + (k >> 6) * C::A_REG + tc::sw128_offset(row, k & 63)) =
+          __double2bfloat16(v);
+    }
+  }
+  tc::fence_proxy_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t num_tiles = (prm.p + TM - 1) / TM;
+  const int my_tiles = (int)((num_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int flush = ex.flush;
+  volatile int* abortv = abort_flag;
+  int no_abort = 0;
+  auto fail = [&]() {
+    stmf_set_status(prm.status, STMF_ETIMEOUT);
+    *abortv = 1;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
+        for (int h = 0; h < nsub; ++h) {
+          const int slot = issued % R;
+          if (!tc::mbar_wait_sleep(&empty[slot], ((issued / R) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[slot], SUB_BYTES);
+          unsigned char* dst = sV + size_t(slot) * SUB_BYTES;
+          tc::tma_load_2d(dst, &tmap, 64 * h, (int32_t)(tile * TM), &full[slot]);
+          tc::tma_load_2d(dst + REG_BYTES, &tmap, 64 * h + 32, (int32_t)(tile * TM), &full[slot]);
+          ++issued;
+        }
+      }
+      // wait for the last copy issued into each slot (already complete unless we aborted)
+      for (int k = issued > R ? issued - R : 0; k < issued; ++k)
+        tc::mbar_wait_sleep(&full[k % R], (k / R) & 1, &no_abort, WAIT_LIMIT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA1 issuer
+    // Z(t) = sum over sub-stages of b1 A_split(h) (accumulator h % 2) and b2 [A1, A2](h) (the
+    // third accumulator), as each sub-stage is split and the Z buffer has been read.
+    if (lane == 0) {
+      const uint32_t idesc_b1 = tc::idesc_bf16(128, N1, 0, 0);
+      const uint32_t idesc_b2 = tc::idesc_bf16(128, C::NB2, 0, 0);
+      // Shared-memory descriptors are linear in the operand address (its 16-byte units sit in
+      // the low bits and every address here is below 256 KB): one base per operand plus
+      // (byte offset >> 4), so the issuing thread spends one add per MMA.
+      const uint64_t vdesc0 = tc::sdesc_sw128(tc::smem_addr(sV), 16, 1024);
+      const uint64_t adesc0 = tc::sdesc_sw128(tc::smem_addr(sA), 16, 1024);
+      bool ok = true;
+      int seq = 0;
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        const int zb = t % ZBUF;
+        ok = tc::mbar_wait_sleep(&zempty[zb], ((t / ZBUF) & 1) ^ 1, abortv, WAIT_LIMIT);
+        uint32_t written = 0;
+        for (int h = 0; h < nsub && ok; ++h, ++seq) {
+          const int slot = seq % R;
+          ok = tc::mbar_wait_sleep(&conv[slot], (seq / R) & 1, abortv, WAIT_LIMIT);
+          if (!ok) break;
+          tc::tc_fence_after();
+          const uint64_t vd = vdesc0 + uint64_t((uint32_t(slot) * SUB_BYTES) >> 4);
+          const uint64_t ad0 = adesc0 + uint64_t((uint32_t(h) * C::A_REG) >> 4);
+          // K step kk of region g: kk = 0, 1 are b1, kk = 2, 3 b2, of features 32g + 16 (kk % 2)
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            const int acc = part == 0 ? (h & 1) : 2;
+            const uint32_t dZ = tmem + uint32_t(zb * C::ZBS + acc * ZS);
+            const uint32_t idesc = part == 0 ? idesc_b1 : idesc_b2;
+            const uint32_t first = (written >> acc) & 1u;
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk)
+                tc::mma_bf16(dZ, vd + uint64_t((g * REG_BYTES + (2 * part + kk) * 32) >> 4),
+                             ad0 + uint64_t(((2 * g + kk) * 32) >> 4), idesc,
+                             (g | kk) ? 1u : first);
+            written |= 1u << acc;
+          }
+        }
+        if (!ok) break;
+        tc::mma_commit(&zfull[zb]);
+      }
+      if (!ok) fail();
+      tc::mma_commit(&mma_done[0]);
+      tc::mbar_wait_sleep(&mma_done[0], 0, &no_abort, WAIT_LIMIT);
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------------ MMA2 issuer
+    // Y_h += [b1 ; b2]^T [W_hi | W_lo] per sub-stage h once W(t) is written; the completion of
+    // block h frees sub-stage h for the producer.
+    if (lane == 0) {
+      const uint32_t idesc2 = tc::idesc_bf16(128, N2, 1, 0);  // V^T MN-major, W K-major
+      const uint64_t vdesc0 = tc::sdesc_sw128(tc::smem_addr(sV), REG_BYTES, 1024);
+      const uint64_t wdesc0 = tc::sdesc_sw128(tc::smem_addr(sW), 16, 1024);
+      bool ok = true;
+      int seq = 0;
+      for (int t = 0; t < my_tiles; ++t) {
+        const int wb = t % WB;
+        const int period = t / flush, yb = period & 1;
+        const bool first = (t % flush) == 0;
+        if (first) ok = tc::mbar_wait_sleep(&yempty[yb], ((period >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
+        ok = ok && tc::mbar_wait_sleep(&wfull[wb], (t / WB) & 1, abortv, WAIT_LIMIT);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint64_t wd = wdesc0 + uint64_t((uint32_t(wb) * 2 * C::W_REG) >> 4);
+        for (int h = 0; h < nsub; ++h, ++seq) {
+          const int slot = seq % R;
+          const uint64_t vd = vdesc0 + uint64_t((uint32_t(slot) * SUB_BYTES) >> 4);
+          const uint32_t dY = tmem + YB0 + uint32_t((yb * nsub + h) * N2);
+#pragma unroll
+          for (int kk = 0; kk < TM / 16; ++kk)
+            tc::mma_bf16(dY, vd + uint64_t((kk * 2048) >> 4),
+                         wd + uint64_t(((kk >> 2) * C::W_REG + (kk & 3) * 32) >> 4), idesc2,
+                         (first && kk == 0) ? 0u : 1u);
+          tc::mma_commit(&empty[slot]);
+        }
+        tc::mma_commit(&wempty[wb]);
+        if ((t % flush) == flush - 1 || t == my_tiles - 1) tc::mma_commit(&yfull[yb]);
+      }
+      if (!ok) fail();
+      tc::mma_commit(&mma_done[1]);
+      tc::mbar_wait_sleep(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
+    }
+  } else if (tid >= CONV0) {
+    // ------------------------------------------------------------------ FP32 -> BF16 b1 | b2
+    // Thread (g, y) owns row y (sample y of the tile) of region g of every sub-stage. It reads
+    // the 32 FP32 values of that row (16-byte chunk c of row y at chunk position c ^ (y & 7)),
+    // then writes b1 of the 32 features as BF16 chunks 0-3 and b2 as chunks 4-7 of the same row,
+    // in the same swizzle. Only this thread touches the row, so nothing else reads the bytes it
+    // overwrites.
+    const int ct = tid - CONV0;
+    const int y = ct & (TM - 1), rg = ct >> 7;
+    const uint32_t sw = uint32_t(y & 7);
+    bool ok = true;
+    int seq = 0;
+    for (int it = 0; it < my_tiles && ok; ++it) {
+      for (int h = 0; h < nsub; ++h, ++seq) {
+        const int slot = seq % R;
+        if (!tc::mbar_wait_sleep(&full[slot], (seq / R) & 1, abortv, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        unsigned char* row = sV + size_t(slot) * SUB_BYTES + size_t(rg) * REG_BYTES + y * 128;
+        float x[8][4];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 a = *reinterpret_cast<const float4*>(row + ((c ^ sw) << 4));
+          x[c][0] = a.x; x[c][1] = a.y; x[c][2] = a.z; x[c][3] = a.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // features 8k .. 8k + 7 of the region
+          const float v[8] = {x[2 * k][0],     x[2 * k][1],     x[2 * k][2],     x[2 * k][3],
+                              x[2 * k + 1][0], x[2 * k + 1][1], x[2 * k + 1][2], x[2 * k + 1][3]};
+          uint4 hi, lo;
+          split8(v, hi, lo);
+          *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
+          *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[slot]);
+      }
+    }
+    if (!ok) fail();
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int g = (warp - 3) >> 2;
+    const int q = warp & 3;            // TMEM lane quarter this warp may access
+    const int L = 32 * q + lane;       // sample within the tile / row within an MMA2 block
+    const int j0 = g * CPG;
+    const uint32_t lane_off = uint32_t(32 * q) << 16;
+    float wacc[CPG], ws[CPG], wc[CPG], ys[NS][CPG], yc[NS][CPG];
+#pragma unroll
+    for (int c = 0; c < CPG; ++c) {
+      wacc[c] = ws[c] = wc[c] = 0.f;
+#pragma unroll
+      for (int h = 0; h < NS; ++h) ys[h][c] = yc[h][c] = 0.f;
+    }
+    const uint32_t wcol = uint32_t(L >> 6) * C::W_REG;
+    int pending = -1;
+    auto fold = [&](int per, bool force) -> bool {
+      const int yb = per & 1;
+      const uint32_t par = (per >> 1) & 1;
+      if (!tc::mbar_test_wait(&yfull[yb], par)) {
+        if (!force) return true;
+        if (!tc::mbar_wait_sleep(&yfull[yb], par, abortv, WAIT_LIMIT)) return false;
+      }
+      tc::tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < NS; ++h) {
+        if (h < nsub) {
+          float yv[2 * CPG];
+          tmem_load_cols<2 * CPG>(
+              tmem + YB0 + uint32_t((yb * nsub + h) * N2 + 2 * j0) + lane_off, yv);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < CPG; ++c) {
+            kahan_add(ys[h][c], yc[h][c], yv[c]);
+            kahan_add(ys[h][c], yc[h][c], yv[CPG + c]);
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&yempty[yb]);
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) {
+        kahan_add(ws[c], wc[c], wacc[c]);
+        wacc[c] = 0.f;
+      }
+      pending = -1;
+      return true;
+    };
+    bool ok = true;
+    for (int it = 0; it < my_tiles; ++it) {
+      const int wb = it % WB, zb = it % ZBUF;
+      const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
+      const int64_t sidx = tile * TM + L;
+      const float nu_s = sidx < prm.p ? (float)(prm.nu ? prm.nu[sidx] : prm.nu_uniform) : 0.f;
+      if (!tc::mbar_wait_sleep(&zfull[zb], (it / ZBUF) & 1, abortv, WAIT_LIMIT)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      float zsum[CPG];
+      tmem_z<CPG, RP, ZS>(tmem + uint32_t(zb * C::ZBS + j0) + lane_off, nsub > 1, zsum);
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&zempty[zb]);
+      float wv[CPG];
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) {
+        const float zz = zsum[c];
+        const float t = ipow_f(zz, d - 1);
+        wv[c] = nu_s * t;
+        wacc[c] += wv[c] * zz;
+      }
+      if (!tc::mbar_wait_sleep(&wempty[wb], ((it / WB) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+        ok = false;
+        break;
+      }
+      unsigned char* wbuf = sW + size_t(wb) * 2 * C::W_REG + wcol;
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(wv[c]);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(wv[c] - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(2 * j0 + c, L & 63)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(wbuf + tc::sw128_offset(2 * j0 + CPG + c, L & 63)) = lo;
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&wfull[wb]);
+      const bool period_end = (it % flush) == flush - 1 || it == my_tiles - 1;
+      if (period_end && pending >= 0 && !fold(pending, true)) {
+        ok = false;
+        break;
+      }
+      if (period_end) pending = it / flush;
+      if (pending >= 0) {
+        const bool force = it == my_tiles - 1 || (it % flush) == flush - 2;
+        if (!fold(pending, force)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    // Lane quarter q of MMA2 block h holds part q % 2 (b1, b2) of features
+    // 64h + 32 (q / 2) + lane: the b2 quarters pass their sums to the b1 quarters of the same
+    // warpgroup through shared memory (the ring is idle by now: every copy has landed and every
+    // MMA has completed once the last fold is done). Every epilogue thread reaches the barrier,
+    // also after a failed wait.
+    const int fi = 32 * (q >> 1) + lane;  // feature within the sub-stage
+    double* xch = reinterpret_cast<double*>(sV);  // [NS][64][RP]
+    if (ok && (q & 1)) {
+#pragma unroll
+      for (int h = 0; h < NS; ++h)
+        if (h < nsub) {
+#pragma unroll
+          for (int c = 0; c < CPG; ++c)
+            xch[(h * 64 + fi) * RP + j0 + c] = (double)ys[h][c] - (double)yc[h][c];
+        }
+    }
+    epi_barrier();
+    if (!ok) {
+      fail();
+    } else {
+      double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+      // First-order correction of w for the split of A (as in the BF16 pass):
+      // sum nu z^d = sum nu z^^d + d sum_i Y_ij dA_ij + O(|dA|^2) with z^ from A1 + A2 + A3.
+      double corr[CPG];
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) corr[c] = 0.0;
+      if (!(q & 1)) {
+#pragma unroll
+        for (int h = 0; h < NS; ++h) {
+          const int i = 64 * h + fi;
+          if (h < nsub && i < n) {
+#pragma unroll
+            for (int c = 0; c < CPG; ++c)
+              if (j0 + c < r) {
+                const double y = ((double)ys[h][c] - (double)yc[h][c]) + xch[(h * 64 + fi) * RP + j0 + c];
+                part[r + i + size_t(n) * (j0 + c)] = y;
+                const double a = prm.A[i + size_t(n) * (j0 + c)];
+                const double a1 = (double)__bfloat162float(__double2bfloat16(a));
+                const double a2 = (double)__bfloat162float(__double2bfloat16(a - a1));
+                const double a3 = (double)__bfloat162float(__double2bfloat16(a - a1 - a2));
+                corr[c] += y * (((a - a1) - a2) - a3);
+              }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) {
+        double x = (double)ws[c] - (double)wc[c] + double(d) * corr[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wred[q * RP + j0 + c] = x;
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (tid < r && !*abortv) {
+    double* part = prm.partials + size_t(blockIdx.x) * (size_t(r) + size_t(n) * r);
+    part[tid] = wred[0 * RP + tid] + wred[1 * RP + tid] + wred[2 * RP + tid] + wred[3 * RP + tid];
+  }
+  if (warp == 1) tc::tmem_dealloc(tmem, ex.tmem_cols);
+}
+
+// ---------------------------------------------------------------------------------- host side
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode32() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+int rp_of(int r) { return r <= 8 ? 8 : 16; }
+
+Tc32Extra plan32(int n, int r) {
+  Tc32Extra ex{};
+  ex.nsub = (n + 63) / 64;
+  const int RP = rp_of(r), N1 = (3 * RP + 15) / 16 * 16, N2 = 2 * RP;
+  // W buffers, A split, 1024 bytes of alignment slack and 1024 of barriers and w sums; a
+  // second W buffer lets the epilogue write W(t+1) while MMA2 still reads W(t), but a deeper
+  // ring matters more: keep six sub-stage slots when the A split of n > 192 needs the room
+  int fixed = 0, R = 0;
+  for (ex.wbufs = 2; ex.wbufs >= 1; --ex.wbufs) {
+    fixed = ex.wbufs * 2 * N2 * 128 + ex.nsub * N1 * 128 + 1024 + 1024;
+    R = (int(kMaxSmem) - fixed) / SUB_BYTES;
+    if (R >= 6) break;
+  }
+  if (ex.wbufs < 1) ex.wbufs = 1;
+  if (R > 8) R = 8;
+  ex.ring = R;
+  ex.flush = 8;
+  const int zbs = 2 * ((N1 + 2 * RP - 1) / (2 * RP) * (2 * RP)) + 2 * RP;
+  ex.zbufs = tmem_need(zbs, 2, ex.nsub, N2) <= 512 ? 2 : 1;
+  const int cols = tmem_need(zbs, ex.zbufs, ex.nsub, N2);
+  int pow2 = 32;
+  while (pow2 < cols) pow2 <<= 1;
+  ex.tmem_cols = pow2;
+  ex.smem_bytes = fixed + R * SUB_BYTES;
+  return ex;
+}
+
+template <int RP, int NS>
+cudaError_t launch32(const CUtensorMap& tmap, const FgParams& prm, const Tc32Extra& ex, int grid,
+                     cudaStream_t s) {
+  const cudaError_t e = smem_limit((const void*)fg_tc32_kernel<RP, NS>, (int)kMaxSmem);
+  if (e != cudaSuccess) return e;
+  return launch_kernel(fg_tc32_kernel<RP, NS>, dim3(grid), dim3(NTHREADS), size_t(ex.smem_bytes),
+                       s, tmap, prm, ex);
+}
+
+template <int RP>
+cudaError_t launch32_ns(const CUtensorMap& tmap, const FgParams& prm, const Tc32Extra& ex,
+                        int grid, cudaStream_t s) {
+  if (ex.nsub == 1) return launch32<RP, 1>(tmap, prm, ex, grid, s);
+  if (ex.nsub == 2) return launch32<RP, 2>(tmap, prm, ex, grid, s);
+  return launch32<RP, 4>(tmap, prm, ex, grid, s);
+}
+
+}  // namespace
+
+bool fg_tc32_supported(int dtype, int n, int r) {
+  if (dtype != STMF_F32) return false;
+  if (r < 1 || r > 16 || n < 1 || n > 64 * MAX_SUB) return false;
+  if (!get_encode32()) return false;
+  const Tc32Extra ex = plan32(n, r);
+  // the exchange at the end of the epilogue reuses the ring: MAX_SUB x 64 x 16 doubles
+  return ex.ring >= ex.nsub && ex.ring * SUB_BYTES >= MAX_SUB * 64 * 16 * 8;
+}
+
+int fg_tc32_grid(int64_t p, int num_sms) {
+  const int64_t tiles = (p + TM - 1) / TM;
+  return (int)(tiles < num_sms ? tiles : num_sms);
+}
+
+cudaError_t fg_tc32_launch(const FgParams& prm, int grid, cudaStream_t s) {
+  if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
+  EncodeFn enc = get_encode32();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
+  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * 4};
+  const cuuint32_t box[2] = {32u, TM};  // 32 FP32 = 128-byte rows
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(prm.V), dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const Tc32Extra ex = plan32(prm.n, prm.r);
+  if (rp_of(prm.r) == 8) return launch32_ns<8>(tmap, prm, ex, grid, s);
+  return launch32_ns<16>(tmap, prm, ex, grid, s);
+}
+
+}  // namespace stmf

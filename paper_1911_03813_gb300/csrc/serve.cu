@@ -293,18 +293,13 @@ extern "C" stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_se
   srv->cfg = *cfg;
   srv->t0 = Clock::now();
   if (cudaSetDevice(cfg->device) != cudaSuccess) return STMF_EINVAL;
-  // the largest workspaces any request may need: FP32 samples take the widest pass grid
-  stmf_samples dummy{};
-  dummy.n = cfg->n_max;
-  dummy.p = int64_t(1) << 30;
-  dummy.ld = (cfg->n_max + 3) / 4 * 4;
-  dummy.dtype = STMF_F32;
+  // the largest workspaces any request may need (every storage type at n_max, r_max)
   const long long Dmax = cfg->r_max + (long long)cfg->n_max * cfg->r_max;
   srv->slots.resize(cfg->max_fits);
   for (auto& s : srv->slots) {
     stmf_status st = stmf_create(cfg->device, &s.ctx);
     if (st != STMF_OK) return st;
-    const size_t ws = stmf::fg_workspace_bytes(s.ctx, &dummy, cfg->r_max);
+    const size_t ws = stmf::fg_workspace_bytes_any(s.ctx, cfg->n_max, cfg->r_max);
     st = stmf::ensure_workspace(s.ctx, ws);
     if (st != STMF_OK) return st;
     const size_t fb = stmf::fit_state_bytes(Dmax, cfg->m_max);

@@ -55,23 +55,17 @@ stmf_status ensure_ws(stmf_ctx* c, size_t bytes) {
 }
 
 struct FgPlan {
-  bool tc = false;   // tensor-core pass (BF16, E4M3)
-  bool f32 = false;  // register-blocked FP32 pass
-  int grid = 0;
+  stmf::PassPlan pass{};
+  bool fits = false;           // some pass holds n x r
   size_t partial_doubles = 0;  // grid * L
   size_t L = 0;
 };
 
-FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
+FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r, bool gather = false) {
   FgPlan pl;
-  const int n = (int)V->n;
-  pl.tc = stmf::fg_tc_supported(V->dtype, n, (int)r) != 0;
-  pl.f32 = !pl.tc && stmf::fg_f32_supported(V->dtype, n, (int)r);
-  pl.grid = pl.tc    ? stmf::fg_tc_grid(V->dtype, n, (int)r, V->p, c->num_sms)
-            : pl.f32 ? stmf::fg_f32_grid(n, V->p, c->num_sms)
-                     : stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
-  pl.L = size_t(r) + size_t(n) * size_t(r);
-  pl.partial_doubles = size_t(pl.grid) * pl.L;
+  pl.fits = stmf::plan_pass(V->dtype, (int)V->n, (int)r, V->p, c->num_sms, gather, &pl.pass);
+  pl.L = size_t(r) + size_t(V->n) * size_t(r);
+  pl.partial_doubles = size_t(pl.pass.grid) * pl.L;
   return pl;
 }
 
@@ -96,6 +90,32 @@ cudaError_t stmf::smem_limit(const void* kernel, int bytes) {
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) done[key] = bytes;
   return e;
+}
+
+bool stmf::plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather,
+                     stmf::PassPlan* out) {
+  PassPlan pl{kPassSimt, 0};
+  if (!gather && fg_tc_supported(dtype, n, r)) {
+    pl = {kPassTc, fg_tc_grid(dtype, n, r, p, num_sms)};
+  } else if (!gather && fg_tc32_supported(dtype, n, r)) {
+    pl = {kPassTc32, fg_tc32_grid(p, num_sms)};
+  } else if (fg_f32_supported(dtype, n, r)) {
+    pl = {kPassF32, fg_f32_grid(n, p, num_sms)};
+  } else {
+    pl = {kPassSimt, fg_simt_grid(dtype, n, r, p, num_sms)};
+  }
+  *out = pl;
+  return pl.kind != kPassSimt || fg_simt_smem(dtype, n, r) <= kMaxSmem;
+}
+
+cudaError_t stmf::launch_pass(const stmf::PassPlan& pl, int dtype, const stmf::FgParams& prm,
+                              cudaStream_t s) {
+  switch (pl.kind) {
+    case kPassTc: return fg_tc_launch(dtype, prm, pl.grid, s);
+    case kPassTc32: return fg_tc32_launch(prm, pl.grid, s);
+    case kPassF32: return fg_f32_launch(prm, pl.grid, s);
+    default: return fg_simt_launch(dtype, prm, pl.grid, s);
+  }
 }
 
 const char* stmf::samples_problem(const stmf_samples* V) {
@@ -124,6 +144,18 @@ stmf_status stmf::ensure_workspace(stmf_ctx* c, size_t bytes) { return ensure_ws
 size_t stmf::fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r) {
   return fg_ws_bytes(plan_fg(c, V, r), r);
 }
+size_t stmf::fg_workspace_bytes_any(const stmf_ctx* c, int64_t n, int64_t r) {
+  size_t most = 0;
+  for (int dt : {STMF_F64, STMF_F32, STMF_BF16, STMF_E4M3}) {
+    stmf_samples V{};
+    V.n = n;
+    V.p = int64_t(1) << 30;
+    V.dtype = dt;
+    const size_t b = fg_ws_bytes(plan_fg(c, &V, r), r);
+    if (b > most) most = b;
+  }
+  return most;
+}
 
 stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double* nu, int d, int64_t r,
                              const double* lambda, const double* A, const double* alpha, double* f,
@@ -142,13 +174,8 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
   if (!lambda || !A || (!yw_out && (!f || !g_lambda || !G_A)))
     return fail(c, STMF_EINVAL, "NULL model or output pointer");
   const int n = (int)V->n;
-  FgPlan pl = plan_fg(c, V, r);
-  if (idx && pl.tc) {  // gathers take the CUDA-core pass
-    pl.tc = false;
-    pl.grid = stmf::fg_simt_grid(V->dtype, n, (int)r, V->p, c->num_sms);
-    pl.partial_doubles = size_t(pl.grid) * pl.L;
-  }
-  if (!pl.tc && !pl.f32 && stmf::fg_simt_smem(V->dtype, n, (int)r) > kMaxSmem)
+  const FgPlan pl = plan_fg(c, V, r, idx != nullptr);  // gathers take the CUDA-core passes
+  if (!pl.fits)
     return fail(c, STMF_EINVAL, "n * r too large for this sample type (shared memory)");
   st = ensure_ws(c, fg_ws_bytes(pl, r));
   if (st != STMF_OK) return st;
@@ -186,15 +213,13 @@ stmf_status stmf::enqueue_fg(stmf_ctx* c, const stmf_samples* V_in, const double
       c->ev_used += 2;
     }
   }
-  cudaError_t e = pl.tc    ? stmf::fg_tc_launch(V->dtype, prm, pl.grid, s)
-                  : pl.f32 ? stmf::fg_f32_launch(prm, pl.grid, s)
-                           : stmf::fg_simt_launch(V->dtype, prm, pl.grid, s);
+  cudaError_t e = stmf::launch_pass(pl.pass, V->dtype, prm, s);
   if (ev_end) cudaEventRecord(ev_end, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused pass launch");
 
   stmf::ModelParams mp{};
   mp.partials = partials;
-  mp.grid = pl.grid;
+  mp.grid = pl.pass.grid;
   mp.A = A;
   mp.lambda = lambda;
   mp.alpha = alpha;

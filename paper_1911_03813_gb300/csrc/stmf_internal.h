@@ -109,6 +109,10 @@ cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s);
 bool fg_f32_supported(int dtype, int n, int r);
 int fg_f32_grid(int n, int64_t p, int num_sms);
 cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s);
+// Tensor-core pass for FP32 samples (each split into two BF16 terms; n <= 256, r <= 16).
+bool fg_tc32_supported(int dtype, int n, int r);
+int fg_tc32_grid(int64_t p, int num_sms);
+cudaError_t fg_tc32_launch(const FgParams& prm, int grid, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
@@ -128,6 +132,18 @@ dim3 norm_sym_grid(long long count, int n, int64_t p, int num_sms);
 size_t norm_sym_slab_bytes(long long count, dim3 grid);
 int norm_sym_square_blocks(long long count);
 cudaError_t norm_sym_launch(int dtype, const SymParams& prm, dim3 grid, cudaStream_t s);
+
+// The fused pass that serves a request: the tensor-core passes (BF16/E4M3, FP32) for n <= 256
+// and r <= 16, else the register-blocked FP32 pass (FP32, r <= 16), else the CUDA-core pass.
+// Gathered rows (an index array) take the CUDA-core passes only.
+enum PassKind { kPassTc = 0, kPassTc32 = 1, kPassF32 = 2, kPassSimt = 3 };
+struct PassPlan {
+  PassKind kind;
+  int grid;
+};
+// false when no pass holds n x r (the CUDA-core pass's shared memory)
+bool plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather, PassPlan* out);
+cudaError_t launch_pass(const PassPlan& pl, int dtype, const FgParams& prm, cudaStream_t s);
 
 inline int elem_bytes(int dtype) {
   switch (dtype) {
@@ -184,6 +200,8 @@ stmf_status enqueue_fg(stmf_ctx* c, const stmf_samples* V, const double* nu, int
                        double* yw_out = nullptr, double nu_uniform = 0.0,
                        bool accumulate = false);
 size_t fg_workspace_bytes(const stmf_ctx* c, const stmf_samples* V, int64_t r);
+// The largest fg_workspace_bytes over every storage type for n features and rank r.
+size_t fg_workspace_bytes_any(const stmf_ctx* c, int64_t n, int64_t r);
 
 // Bytes of the device optimiser state for D unknowns and m pairs.
 size_t fit_state_bytes(long long D, int m);

@@ -83,6 +83,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
+// try_wait that may suspend the thread for up to `hint_ns` nanoseconds (or until the phase
+// completes) instead of returning at once: a waiting warp then takes no issue slots from the
+// warps that are working.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// mbar_wait with suspending probes: gives up after about `limit_cycles` SM clocks or when
+// *abort is set (checked every 16 probes, i.e. at least every 16 x hint_ns).
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                long long limit_cycles, uint32_t hint_ns = 20000) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t k = 1;; ++k) {
+    if (mbar_try_wait_hint(bar, parity, hint_ns)) return true;
+    if ((k & 15) == 0) {
+      if (*abort) return false;
+      if (clock64() - t0 > limit_cycles) return false;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y,
                                             uint64_t* bar) {

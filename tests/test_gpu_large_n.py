@@ -2,8 +2,10 @@
 
 Shapes past the tensor-core passes (n > 256) run on the CUDA cores: 64-sample tiles (32 for FP64
 samples, whose 64-sample tile does not fit in shared memory), the Gram pass staged in feature
-chunks, and the range finder in FP32 when its FP64 tile does not fit. Same tolerances as the
-other parity tests; the FP32 range finder is compared at 1e-5.
+chunks, and the range finder in FP32 when its FP64 tile does not fit. The CUDA-core pass
+multiplies decoded BF16/E4M3 values in FP32, so every storage type but FP64 is held to the FP32
+tolerance, 1e-5 normwise and entry by entry with a floor of 0.01 of the largest entry; the FP32
+range finder is compared at 1e-5.
 """
 
 import numpy as np
@@ -18,7 +20,7 @@ from paper_1911_03813_gb300 import inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 4e-5, "e4m3": 4e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5, "e4m3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -41,6 +43,12 @@ def decoded(st):
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def elementwise(a, b, c):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.max(np.abs(a - b) / (np.abs(b) + c * np.max(np.abs(b)) + 1e-300)))
 
 
 def dev_model(lam, A):
@@ -69,6 +77,8 @@ def test_fg_parity_large_n(stmf, dtype, n, p, r, d):
     assert abs(f.item() - f_ref) <= tol * S
     assert rel(gl.cpu().numpy(), gl_ref) <= tol
     assert rel(GA.cpu().numpy(), GA_ref) <= tol
+    assert elementwise(gl.cpu().numpy(), gl_ref, 0.01) <= tol
+    assert elementwise(GA.cpu().numpy(), GA_ref, 0.01) <= tol
 
 
 @pytest.mark.parametrize("dtype,n,r", [("f64", 512, 32), ("f32", 512, 64)])

@@ -1,12 +1,16 @@
 """GPU parity of the C ABI entry points against the FP64 oracle (run with -m gpu).
 
 Inputs come from the seeded generators; the oracle evaluates Alg. 2 in FP64 on exactly the
-values the GPU reads (BF16 codes widened, E4M3 codes times their scales). Tolerances:
-  FP64 samples   1e-12  (normwise relative for g_lambda and G_A; f relative to the
-                          cancellation scale S = alpha + |lambda^T u| + 2 |w^T lambda|)
-  FP32 samples   1e-5
-  BF16 / E4M3    4e-5   (tensor-core pass: A and W are split into BF16 hi/lo pairs, so the
-                          products carry ~2^-17 relative error before FP32 accumulation)
+values the GPU reads (BF16 codes widened, E4M3 codes times their scales). f is compared against
+the cancellation scale S = alpha + |lambda^T u| + 2 |w^T lambda|; g_lambda and G_A both
+normwise, ||x - x*|| <= tol ||x*||, and entry by entry,
+|x_i - x*_i| <= tol_el (|x*_i| + c max_k |x*_k|), so that a small entry cannot be wrong unseen:
+  FP64 samples   tol 1e-12, tol_el 1e-12, c = 0.01  (measured <= 1.6e-14)
+  FP32 samples   tol 1e-5,  tol_el 1e-5,  c = 0.01  (measured <= 7e-7)
+  BF16 / E4M3    tol 5e-6,  tol_el 1e-5,  c = 0.1   (measured <= 1.8e-6 normwise and 1.7e-6
+                 entry-wise over these shapes; the tensor-core pass splits A and W into BF16
+                 hi/lo pairs, ~2^-17 relative per product, then accumulates in FP32)
+At the full n = 256, p = 2^24 workload the BF16 pass is held to 1e-6 (measured 1.5e-8).
 """
 
 import json
@@ -22,7 +26,8 @@ from paper_1911_03813_gb300 import inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 4e-5, "e4m3": 4e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 5e-6, "e4m3": 5e-6}
+TOL_EL = {"f64": (1e-12, 0.01), "f32": (1e-5, 0.01), "bf16": (1e-5, 0.1), "e4m3": (1e-5, 0.1)}
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +76,7 @@ def report(tag, **vals):
     print("PARITY " + json.dumps(dict(tag=tag, **vals)))
 
 
-def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0, tag=""):
+def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0, tag="", el=None):
     Vd = decoded(st)
     f_ref, gl_ref, GA_ref, parts = oracle.fg_implicit(nu, Vd.T, lam, A, d, alpha=alpha,
                                                       return_parts=True)
@@ -84,6 +89,9 @@ def check_fg(stmf, st, nu, lam, A, d, tol, alpha=0.0, tag=""):
     assert abs(f - f_ref) <= tol * S, (f, f_ref, S)
     assert rel(gl, gl_ref) <= tol, rel(gl, gl_ref)
     assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
+    tol_el, c = el if el is not None else TOL_EL[st["dtype"]]
+    assert elementwise(gl, gl_ref, c) <= tol_el, elementwise(gl, gl_ref, c)
+    assert elementwise(GA, GA_ref, c) <= tol_el, elementwise(GA, GA_ref, c)
     return f, gl, GA
 
 
@@ -117,10 +125,13 @@ def test_fg_parity(stmf, dtype, n, p, r, d):
 
 
 @pytest.mark.parametrize("n,p,r,d", [(64, 777, 7, 4), (65, 777, 7, 4), (128, 4099, 16, 3),
-                                     (129, 2001, 16, 3)])
+                                     (129, 2001, 16, 3), (31, 300001, 1, 3), (32, 1000, 9, 2),
+                                     (192, 100003, 8, 4), (193, 50001, 16, 3),
+                                     (256, 200001, 16, 4), (100, 1000000, 10, 3)])
 def test_fg_f32_tile_boundaries(stmf, n, p, r, d):
-    """The FP32 pass takes 128-sample tiles up to n = 64, 64-sample tiles up to n = 128 and
-    32-sample tiles above: both sides of each boundary, with ragged tails."""
+    """The FP32 tensor-core pass streams each 128-sample tile as ceil(n / 64) sub-stages of 64
+    features through a ring of six: both sides of each sub-stage boundary, r on both sides of
+    8, ragged tails, and enough tiles per block that the ring wraps many times."""
     data = inputs.gmm(n, p, min(r, 8), 0.1, seed=n + p + r + d)
     lam, A = inputs.random_model(n, r, seed=3 * r + d)
     st = inputs.to_storage(data["V"], "f32", device="cuda")
@@ -237,12 +248,13 @@ def test_fg_full_size(stmf, dtype, n, p, r, d, sigma):
     f_ref, gl_ref, GA_ref, parts = _oracle_on_device_storage(st, lam, A, d)
     f, gl, GA = run_fg(stmf, st, None, lam, A, d)
     S = abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
-    tol = TOL[dtype]
+    tol = 1e-6 if dtype == "bf16" else TOL[dtype]
     print(f"\nfull size {dtype} sigma={sigma}: f err/S {abs(f - f_ref) / S:.2e}, "
           f"g_lambda {rel(gl, gl_ref):.2e}, G_A {rel(GA, GA_ref):.2e}")
     assert abs(f - f_ref) <= tol * S, (f, f_ref, S)
     assert rel(gl, gl_ref) <= tol, rel(gl, gl_ref)
     assert rel(GA, GA_ref) <= tol, rel(GA, GA_ref)
+    assert elementwise(GA, GA_ref, 0.1) <= 10 * tol and elementwise(gl, gl_ref, 0.1) <= 10 * tol
     del st
     torch.cuda.empty_cache()
 
@@ -288,9 +300,9 @@ def test_sharded_partials_on_one_gpu(stmf, dtype, tol):
     assert float(torch.linalg.norm(gl1 - gl0) / torch.linalg.norm(gl0)) <= tol
 
 
-@pytest.mark.parametrize("dtype,n,p,r,d,tol", [("bf16", 256, 600000, 16, 4, 4e-5),
+@pytest.mark.parametrize("dtype,n,p,r,d,tol", [("bf16", 256, 600000, 16, 4, 5e-6),
                                                ("f64", 30, 70001, 3, 3, 1e-12),
-                                               ("e4m3", 64, 300000, 8, 3, 4e-5)])
+                                               ("e4m3", 64, 300000, 8, 3, 5e-6)])
 def test_fg_host_streaming(stmf, dtype, n, p, r, d, tol):
     """Host inputs streamed in chunks (several chunks at these sizes for 1-byte and 2-byte
     samples) give the oracle's result."""
@@ -340,7 +352,9 @@ def test_fg_near_fit(stmf, dtype, sigma):
 def test_fg_e4m3_every_code(stmf, d):
     """Every finite E4M3 code (normals, subnormals, both zeros) goes through the tensor-core
     pass's widening to BF16: each sample holds all 254 finite codes in a seeded order, with
-    seeded per-sample scales."""
+    seeded per-sample scales. Entries spanning 2^-9 .. 448 within one sample make z = q^T a
+    cancel far more than Gaussian samples do, so this case is held to 1e-5 normwise and entry
+    by entry against the largest entry (measured 4.0e-6 and 3.2e-6)."""
     n, p, r = 254, 1000, 16
     codes = np.array([c for c in range(256) if c not in (0x7F, 0xFF)], dtype=np.uint8)
     g = inputs.rng(254)
@@ -352,4 +366,4 @@ def test_fg_e4m3_every_code(stmf, d):
     st = dict(data=torch.from_numpy(bits).view(torch.float8_e4m3fn).cuda(),
               scale=torch.from_numpy(scale).cuda(), n=n, ld=ld, dtype="e4m3")
     lam, A = inputs.random_model(n, r, seed=255)
-    check_fg(stmf, st, None, lam, A, d, TOL["e4m3"])
+    check_fg(stmf, st, None, lam, A, d, 1e-5, el=(1e-5, 1.0))
