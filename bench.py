@@ -89,6 +89,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class UtilSampler:
+    """nvidia-smi utilization.gpu (percent of the sample period in which a kernel ran) sampled
+    every 100 ms while the block runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.values = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=utilization.gpu",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            try:
+                self.values.append(float(line.strip()))
+            except ValueError:
+                pass
+
+    def mean(self):
+        return statistics.mean(self.values) if self.values else None
+
+
 def strip_comments(src):
     """C/C++/CUDA source without its comments and blank lines (string and character literals
     kept as they are), so that a comment-only edit leaves the code hash unchanged."""
@@ -114,10 +152,10 @@ def strip_comments(src):
     return "\n".join(line for line in lines if line)
 
 
-def kernel_source_hash():
-    """Hash of the fused tensor-core pass's code (comments excluded)."""
+def kernel_source_hash(files=("fg_tc.cu", "tc_common.cuh")):
+    """Hash of a fused pass's code (comments excluded)."""
     h = hashlib.sha256()
-    for f in ("fg_tc.cu", "tc_common.cuh"):
+    for f in files:
         p = os.path.join(ROOT, "paper_1911_03813_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(strip_comments(open(p, encoding="utf-8").read()).encode())
@@ -134,7 +172,8 @@ def ncu_traffic(kernel_tag):
         t = json.load(open(path)).get(kernel_tag)
     except ValueError:
         return None
-    if not t or t.get("source_hash") != kernel_source_hash():
+    files = tuple(t.get("sources", ("fg_tc.cu", "tc_common.cuh"))) if t else ()
+    if not t or t.get("source_hash") != kernel_source_hash(files):
         return None
     return t.get("dram_bytes_per_launch_full")
 
@@ -178,6 +217,19 @@ def cpu_baseline(dev, seconds=12.0, p_sample=1 << 17):
                                           "g_lambda": rel(got[1], ref64[1]),
                                           "G_A": rel(got[2], ref64[2])}}
         del st
+    k, el = oracle_time(Vt, lam, A, seconds)
+    per_eval_full = el / k * (P_FULL / p_sample)
+    cores = len(os.sched_getaffinity(0))
+    one = one_core_oracle(p_sample, seconds / 2)
+    return dict(value=1.0 / per_eval_full, unit="evals/s", cores=cores, kind="oracle",
+                sample="%d of %d samples (n=%d, d=%d, r=%d), %d evaluations in %.1f s, scaled "
+                       "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el),
+                one_core=one, accuracy=accuracy)
+
+
+def oracle_time(Vt, lam, A, seconds):
+    """(evaluations, seconds) of the FP64 oracle repeated for about `seconds`."""
+    import oracle
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -185,42 +237,75 @@ def cpu_baseline(dev, seconds=12.0, p_sample=1 << 17):
         k += 1
         el = time.perf_counter() - t0
         if el >= seconds:
-            break
-    per_eval_sample = el / k
-    per_eval_full = per_eval_sample * (P_FULL / p_sample)
-    cores = len(os.sched_getaffinity(0))
-    return dict(value=1.0 / per_eval_full, unit="evals/s", cores=cores, kind="oracle",
-                sample="%d of %d samples (n=%d, d=%d, r=%d), %d evaluations in %.1f s, scaled "
-                       "by p" % (p_sample, P_FULL, N_FEAT, D, R, k, el),
-                accuracy=accuracy)
+            return k, el
 
 
-def make_requests(count, seed, dev):
+def one_core_oracle(p_sample, seconds):
+    """The same oracle timing in a fresh process restricted to one core (affinity and every BLAS
+    thread count set to 1 before NumPy loads), scaled to the whole workload like the all-core
+    figure."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core",
+                              str(p_sample), str(seconds)], env=env, capture_output=True,
+                             text=True, timeout=600)
+        res = json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": str(e)[:200]}
+    per_full = res["seconds"] / res["evals"] * (P_FULL / p_sample)
+    return {"value": 1.0 / per_full, "unit": "evals/s", "cores": 1,
+            "sample": "%d of %d samples, %d evaluations in %.1f s on one core, scaled by p"
+                      % (p_sample, P_FULL, res["evals"], res["seconds"])}
+
+
+def oracle_one_core_main(p_sample, seconds):
+    os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    import numpy as np
+
+    from paper_1911_03813_gb300 import inputs
+    data = inputs.gmm(N_FEAT, p_sample, N_MEANS, SIGMA, seed=SEED)
+    Vt = np.ascontiguousarray(data["V"].T)
+    lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
+    k, el = oracle_time(Vt, lam, A, seconds)
+    print(json.dumps({"evals": k, "seconds": el}), flush=True)
+
+
+def make_requests(count, seed, dev, pool=256):
     """Serving requests: n, p log-uniform in [8, 128] x [1e3, 1e6], d in {3, 4}, r in [1, 16],
-    sigma log-uniform in [1e-4, 1e-1], four seeded starts each; samples in pinned host memory
-    (BF16), generated on the device and copied once before the clock starts."""
+    sigma log-uniform in [1e-4, 1e-1], four seeded starts each. The samples come from a pool of
+    `pool` seeded Gaussian-mixture sets in pinned host memory (BF16; generated on the device and
+    copied once before the clock starts), request k taking set k % pool: 4096 distinct sets of
+    this size would hold about 50 GB of pinned host memory. Each request still carries its own
+    d, r and starts, and the server copies its samples to the device at admission."""
     import numpy as np
     import torch
 
     from paper_1911_03813_gb300 import inputs
     g = np.random.default_rng(seed)
-    out = []
-    for k in range(count):
+    sets = []
+    for k in range(min(count, pool)):
         n = int(round(np.exp(g.uniform(np.log(8), np.log(128)))))
         p = int(round(np.exp(g.uniform(np.log(1e3), np.log(1e6)))))
-        d = int(g.integers(3, 5))
-        r = int(g.integers(1, 17))
         sigma = float(np.exp(g.uniform(np.log(1e-4), np.log(1e-1))))
-        st = inputs.gmm_device(n, p, r, sigma, seed * 100003 + k, dev, out_dtype="bf16")
+        st = inputs.gmm_device(n, p, 16, sigma, seed * 100003 + k, dev, out_dtype="bf16")
         host = torch.empty(st["data"].shape, dtype=torch.int16, pin_memory=True)
         host.copy_(st["data"].view(torch.int16))
+        sets.append(dict(V=dict(data=host.numpy(), n=n, dtype="bf16"), n=n, p=p, keep=host))
+        del st
+    out = []
+    for k in range(count):
+        s_ = sets[k % len(sets)]
+        n = s_["n"]
+        d = int(g.integers(3, 5))
+        r = int(g.integers(1, 17))
         x0 = []
         for s in range(4):
             lam0, A0 = inputs.random_model(n, r, seed=seed * 7919 + 4 * k + s, lam="equal")
             x0.append(np.concatenate([lam0, A0.reshape(-1, order="F")]))
-        out.append(dict(V=dict(data=host.numpy(), n=n, dtype="bf16"), x0=np.array(x0), d=d,
-                        n_=n, p=p, r=r, keep=host))
-        del st
+        out.append(dict(V=s_["V"], x0=np.array(x0), d=d, n_=n, p=s_["p"], r=r, keep=s_["keep"]))
     return out
 
 
@@ -232,7 +317,7 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
 
     from paper_1911_03813_gb300 import stmf
     opts = dict(pgtol=1e-5, factr=1e9, max_evals=200, alpha_mode=0, chunk=8)
-    sat = make_requests(max(n_requests // 2, 8), seed, dev)
+    sat = make_requests(max(n_requests // 4, 8), seed, dev)
     poi = make_requests(n_requests, seed + 1, dev)
 
     def poisson(srv, rate, draw_seed):
@@ -254,13 +339,16 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
 
     with stmf.Server(device=device_index, max_fits=64, n_max=128, r_max=16, m_max=5,
                      mem_budget=150 << 30) as srv:
-        t0 = time.perf_counter()
-        tick = [srv.submit(q["V"], q["d"], q["x0"], **opts) for q in sat]
-        for t in tick:
-            srv.poll(t)
-        t_sat = time.perf_counter() - t0
+        with UtilSampler(device_index) as u_sat:
+            t0 = time.perf_counter()
+            tick = [srv.submit(q["V"], q["d"], q["x0"], **opts) for q in sat]
+            for t in tick:
+                srv.poll(t)
+            t_sat = time.perf_counter() - t0
         rate_sat = len(sat) / t_sat
-        main = poisson(srv, 0.8 * rate_sat, seed + 2)
+        with UtilSampler(device_index) as u_poi:
+            main = poisson(srv, 0.8 * rate_sat, seed + 2)
+        main["gpu_busy_pct"] = u_poi.mean()
         extra = []
         for k, mult in enumerate(sweep):
             row = poisson(srv, mult * rate_sat, seed + 3 + k)
@@ -269,8 +357,13 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
         stats = srv.stats()
     out = {"requests": len(poi), "starts_per_request": 4,
            "workload": "n, p log-uniform in [8,128] x [1e3,1e6], d in {3,4}, r in [1,16], "
-                       "sigma log-uniform in [1e-4,1e-1], BF16 samples on the host",
+                       "sigma log-uniform in [1e-4,1e-1], BF16 samples on the host (a pool of "
+                       "256 seeded sample sets, request k using set k mod 256)",
+           "saturated_requests": len(sat),
            "saturated_requests_per_s": rate_sat, "saturated_fits_per_s": 4 * rate_sat,
+           "saturated_gpu_busy_pct": u_sat.mean(),
+           "gpu_busy": "nvidia-smi utilization.gpu (share of time some kernel ran), mean of "
+                       "100 ms samples over the run",
            **main,
            "peak_admitted_bytes": int(stats["peak_bytes_in_use"]),
            "optimiser": "L-BFGS m=5, pgtol 1e-5, factr 1e9, <= 200 evaluations per start"}
@@ -307,9 +400,10 @@ def gram_bench(dev):
 
 
 def alpha_bench(dev):
-    """||X||^2 at the FP32 scale workload (n=100, p=2.5e6, 10 means, d=3): the method stmf_norm_x
-    picks (the distinct entries of the symmetric X) against the Gram form, whose time is
-    extrapolated from a 2^16-sample slice by (p / 2^16)^2."""
+    """||X||^2 at the FP32 scale workload (n=100, p=2.5e6, 10 means, d=3), two real passes over
+    all 2.5e6 samples: the method stmf_norm_x picks for FP32 samples (the distinct entries of the
+    symmetric X), and the Gram form nu^T (V^T V)^d nu on the tensor cores over the BF16 copy of
+    the same samples (the BF16 values, so its alpha differs from the FP32 one by the rounding)."""
     import torch
 
     from paper_1911_03813_gb300 import inputs, stmf
@@ -321,18 +415,29 @@ def alpha_bench(dev):
     a = stmf.norm_x(st, None, d)
     torch.cuda.synchronize()
     t_auto = time.perf_counter() - t0
-    sl = dict(st)
-    sl["data"] = st["data"][: 1 << 16]
-    stmf.norm_x(sl, None, d, method="gram")
+    ld16 = inputs.padded_ld(n, "bf16")
+    data16 = torch.zeros((p, ld16), dtype=torch.bfloat16, device=dev)
+    data16[:, :n] = st["data"][:, :n]
+    st16 = dict(st, data=data16, dtype="bf16", ld=ld16)
+    del st
+    torch.cuda.empty_cache()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g = stmf.norm_x(st16, None, d, method="gram")
+    e1.record()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    stmf.norm_x(sl, None, d, method="gram")
-    torch.cuda.synchronize()
-    t_gram = (time.perf_counter() - t0) * (p / (1 << 16)) ** 2
-    del st, sl
-    return {"n": n, "p": p, "d": d, "dtype": "f32", "method": "compressed symmetric X",
-            "s": t_auto, "gram_s_extrapolated": t_gram, "speedup": t_gram / t_auto,
-            "alpha": a.item()}
+    ms_gram = e0.elapsed_time(e1)
+    T = (p + 127) // 128
+    flop = 2.0 * 128 * 128 * n * T * (T + 1) / 2
+    del st16
+    return {"n": n, "p": p, "d": d,
+            "compressed_fp32": {"method": "distinct entries of the symmetric X (FP32 samples)",
+                                "s": t_auto, "alpha": a.item()},
+            "gram_bf16_tensor_cores": {"method": "Gram form over all sample pairs (BF16 copy)",
+                                       "s": ms_gram / 1e3, "alpha": g.item(),
+                                       "tflops": flop / (ms_gram / 1e3) / 1e12,
+                                       "flop_counted": "2*128*128*n per computed 128x128 tile "
+                                                       "pair, upper triangle"}}
 
 
 def fp32_scale_bench(dev, evals=1000):
@@ -415,6 +520,10 @@ def workload_config(P, world):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores. Each step is one evaluation of Alg. 2 on a bounded
+    sample of the workload (the first 2^16 of its 2^24 samples, the same seeded mixture):
+    ms_per_step is the measured time of that step, and value converts it to evaluations of the
+    whole workload per second by the ratio of samples (the evaluation is linear in p)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -433,17 +542,20 @@ def run_reference(args):
     for _ in range(steps):
         oracle.fg_implicit(None, Vt, lam, A, D)
     el = time.perf_counter() - t0
-    per_full = el / steps * (P_FULL / p_sample)
-    v = 1.0 / per_full
+    step_s = el / steps
+    v = (p_sample / P_FULL) / step_s
+    cfg = workload_config(P_FULL, 1)
+    cfg["timed_sample_p"] = p_sample
+    sample = ("each step: the FP64 oracle (NumPy) on the first %d of the %d samples; value = "
+              "evaluations of the whole workload per second = (%d / %d) / step time"
+              % (p_sample, P_FULL, p_sample, P_FULL))
     line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "evals/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
-            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(P_FULL, 1),
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": len(os.sched_getaffinity(0)),
-                             "kind": "oracle",
-                             "sample": "FP64 oracle (NumPy) on %d of %d samples per step, "
-                                       "scaled by p" % (p_sample, P_FULL)},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -462,7 +574,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=P_FULL)
-    ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--serving-requests", type=int, default=4096)
     ap.add_argument("--no-gram", action="store_true")
     ap.add_argument("--serving-sweep", default="",
                     help="comma-separated multiples of the saturated serving rate to run after "
@@ -477,7 +589,11 @@ def main():
                     help="time only the ||X||^2 Gram pass on 2^16 samples and print it")
     ap.add_argument("--legs", default="bf16,fp32,fp8",
                     help="sample types to time (bf16 is the headline)")
+    ap.add_argument("--oracle-one-core", nargs=2, type=float, default=None,
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_one_core:
+        return oracle_one_core_main(int(args.oracle_one_core[0]), args.oracle_one_core[1])
     if args.impl == "reference":
         return run_reference(args)
 
@@ -594,10 +710,6 @@ def main():
     peaks = measured_peaks()
     ach16 = bytes16 / (pass16 / 1e3) / 1e9
     ach32 = bytes32 / (pass32 / 1e3) / 1e9
-    # the FP32 pass is bound by the FP32 pipe: Z = V^T A and Y += V W are 2 n r FMA per sample
-    flop32 = 4 * P * N_FEAT * R
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
 
     # end to end through the public API with host buffers: stmf_fg_host streams V from pinned
     # host memory in chunks (copies overlapped with the passes) and returns f and g to the host
@@ -671,12 +783,13 @@ def main():
         "fp32": {"value": steps32 / (ms32 / 1e3) * world, "unit": "evals/s",
                  "ms_per_step": ms32 / steps32, "hbm_gbs_over_V": bytes32 / (ms32 / steps32 / 1e3) / 1e9,
                  "pass_frac_of_hbm": ach32 / peaks["hbm_gbs"],
-                 "roofline": {"bound": "alu", "achieved": flop32 / (pass32 / 1e3) / 1e12,
-                              "peak": fp32_peak, "unit": "TFLOP/s",
-                              "frac": flop32 / (pass32 / 1e3) / 1e12 / fp32_peak,
-                              "traffic": None, "kernel": "fused pass, FP32 samples (CUDA cores)",
-                              "peak_src": "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
-                              "algorithmic_flop_per_launch": flop32},
+                 "roofline": {"bound": "hbm", "achieved": ach32, "peak": peaks["hbm_gbs"],
+                              "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
+                              "traffic": ncu_traffic("fg_pass_f32"),
+                              "kernel": "fused pass, FP32 samples (tensor cores, in-place "
+                                        "BF16 hi/lo split)",
+                              "peak_src": peaks["src"],
+                              "algorithmic_bytes_per_launch": bytes32},
                  "bf16_over_fp32": (args.steps / ms16) / (steps32 / ms32)},
         "fp8": {"value": args.steps / (ms8 / 1e3) * world, "unit": "evals/s",
                 "ms_per_step": ms8 / args.steps,

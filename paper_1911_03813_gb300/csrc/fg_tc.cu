@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     const int L = 32 * q + lane;       // sample within the tile / feature within the M-block
     const int j0 = g * CPG;
     const uint32_t lane_off = uint32_t(32 * q) << 16;
-    // per-period FP32 sums of w are folded with the Y periods into compensated FP32 totals
+    // per-period FP32 sums of w join compensated FP32 totals at the end of each period
     float wacc[CPG], ws[CPG], wc[CPG], ys[2][CPG], yc[2][CPG];
 #pragma unroll
     for (int c = 0; c < CPG; ++c) {
@@ -421,11 +421,6 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&yempty[yb]);
-#pragma unroll
-      for (int c = 0; c < CPG; ++c) {
-        kahan_add(ws[c], wc[c], wacc[c]);
-        wacc[c] = 0.f;
-      }
       pending = -1;
       return true;
     };
@@ -491,6 +486,16 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       // is still outstanding is forced on the tile before the next period ends, at a period's
       // end if one is somehow still pending, and on the CTA's last tile.
       const bool period_end = (it % flush) == flush - 1 || it == my_tiles - 1;
+      // the FP32 sum of w over the period joins the compensated total at the period's last
+      // tile, a fixed point (the Y fold below happens whenever MMA2 is done, which varies), so
+      // the result is the same bit for bit from run to run
+      if (period_end) {
+#pragma unroll
+        for (int c = 0; c < CPG; ++c) {
+          kahan_add(ws[c], wc[c], wacc[c]);
+          wacc[c] = 0.f;
+        }
+      }
       if (period_end && pending >= 0 && !fold(pending, true)) {
         ok = false;
         break;

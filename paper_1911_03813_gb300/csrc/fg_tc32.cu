@@ -29,13 +29,12 @@
 // So each K step of 16 of MMA1 is either all b1 or all b2, and the rows of MMA2 block h are
 // [b1 f0-31; b2 f0-31; b1 f32-63; b2 f32-63] of sub-stage h's features.
 //
-// Warp roles (864 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
+// Warp roles (736 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
 // warp 2 = MMA2 issuer, warps 3-18 = epilogue (four warpgroups that split the components;
-// thread = TMEM lane = sample of the tile, or row of an MMA2 block), warps 19-26 = converters
-// (thread = one row of one region, so the in-place rewrite never crosses threads; eight warps,
-// two per scheduler, keep the conversion's dependent arithmetic off the critical path). Every
-// wait is bounded: a wait that runs out sets STMF_ETIMEOUT in the status word and all roles
-// wind down, wait for their own copies and MMAs, and free TMEM.
+// thread = TMEM lane = sample of the tile, or row of an MMA2 block), warps 19-22 = converters
+// (thread = one sample row of both regions, so the in-place rewrite never crosses threads).
+// Every wait is bounded: a wait that runs out sets STMF_ETIMEOUT in the status word and all
+// roles wind down, wait for their own copies and MMAs, and free TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -51,7 +50,7 @@ constexpr int SUB_BYTES = 2 * REG_BYTES; // one sub-stage: 64 FP32 features of 1
 constexpr int MAX_SUB = 4;               // n <= 256
 constexpr int EG = 4;                    // epilogue warpgroups
 constexpr int NEPI = 128 * EG;
-constexpr int NCONV = 8;                 // converter warps: 128 rows x 2 regions
+constexpr int NCONV = 4;                 // converter warps: one thread per sample row
 constexpr int CONV0 = 96 + NEPI;         // first converter thread
 constexpr int NTHREADS = CONV0 + 32 * NCONV;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
@@ -120,22 +119,45 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 // z of one warpgroup's CPG components from a Z buffer at `zaddr`: the b2 accumulator's two
 // terms, the second b1 accumulator's three (when there is more than one sub-stage) and the
 // first's three, each accumulator's terms summed smallest first, in FP32 rounded to nearest.
-template <int CPG, int RP, int ZS>
+// ONE_BY_ONE reads the accumulators one at a time (three waits instead of one) so that at most
+// three terms are live: the variant for n > 192 keeps four blocks of Y sums in registers.
+template <int CPG, int RP, int ZS, bool ONE_BY_ONE>
 __device__ __forceinline__ void tmem_z(uint32_t zaddr, bool two_b1, float (&z)[CPG]) {
-  float v[8][CPG];
+  if constexpr (ONE_BY_ONE) {
+    float v[3][CPG];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(k * RP), v[k]);
+    for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[k]);
+    tc::tmem_ld_wait();
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (two_b1) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[3 + k]);
+    for (int c = 0; c < CPG; ++c) z[c] = v[1][c] + v[0][c];
+    if (two_b1) {
 #pragma unroll
-  for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[6 + k]);
-  tc::tmem_ld_wait();
+      for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[k]);
+      tc::tmem_ld_wait();
 #pragma unroll
-  for (int c = 0; c < CPG; ++c) {
-    float t = v[7][c] + v[6][c];
-    if (two_b1) t += (v[5][c] + v[4][c]) + v[3][c];
-    z[c] = t + ((v[2][c] + v[1][c]) + v[0][c]);
+      for (int c = 0; c < CPG; ++c) z[c] += (v[2][c] + v[1][c]) + v[0][c];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(k * RP), v[k]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < CPG; ++c) z[c] += (v[2][c] + v[1][c]) + v[0][c];
+  } else {
+    float v[8][CPG];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(k * RP), v[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (two_b1) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[3 + k]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[6 + k]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < CPG; ++c) {
+      float t = v[7][c] + v[6][c];
+      if (two_b1) t += (v[5][c] + v[4][c]) + v[3][c];
+      z[c] = t + ((v[2][c] + v[1][c]) + v[0][c]);
+    }
   }
 }
 
@@ -365,13 +387,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (tid >= CONV0) {
     // ------------------------------------------------------------------ FP32 -> BF16 b1 | b2
-    // Thread (g, y) owns row y (sample y of the tile) of region g of every sub-stage. It reads
-    // the 32 FP32 values of that row (16-byte chunk c of row y at chunk position c ^ (y & 7)),
-    // then writes b1 of the 32 features as BF16 chunks 0-3 and b2 as chunks 4-7 of the same row,
-    // in the same swizzle. Only this thread touches the row, so nothing else reads the bytes it
-    // overwrites.
-    const int ct = tid - CONV0;
-    const int y = ct & (TM - 1), rg = ct >> 7;
+    // Thread y owns row y (sample y of the tile) of both regions of every sub-stage. Per region
+    // it reads the 32 FP32 values of its row (16-byte chunk c of row y at chunk position
+    // c ^ (y & 7)), then writes b1 of the 32 features as BF16 chunks 0-3 and b2 as chunks 4-7 of
+    // the same row, in the same swizzle. Only this thread touches the row, so nothing else reads
+    // the bytes it overwrites.
+    const int y = tid - CONV0;
     const uint32_t sw = uint32_t(y & 7);
     bool ok = true;
     int seq = 0;
@@ -382,6 +403,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ok = false;
           break;
         }
+#pragma unroll 1
+        for (int rg = 0; rg < 2; ++rg) {
         unsigned char* row = sV + size_t(slot) * SUB_BYTES + size_t(rg) * REG_BYTES + y * 128;
         float x[8][4];
 #pragma unroll
@@ -397,6 +420,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           split8(v, hi, lo);
           *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
           *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
+        }
         }
         tc::fence_proxy_async_smem();
         __syncwarp();
@@ -445,11 +469,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&yempty[yb]);
-#pragma unroll
-      for (int c = 0; c < CPG; ++c) {
-        kahan_add(ws[c], wc[c], wacc[c]);
-        wacc[c] = 0.f;
-      }
       pending = -1;
       return true;
     };
@@ -465,7 +484,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc::tc_fence_after();
       float zsum[CPG];
-      tmem_z<CPG, RP, ZS>(tmem + uint32_t(zb * C::ZBS + j0) + lane_off, nsub > 1, zsum);
+      tmem_z<CPG, RP, ZS, (NS > 2)>(tmem + uint32_t(zb * C::ZBS + j0) + lane_off, nsub > 1, zsum);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&zempty[zb]);
@@ -493,6 +512,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&wfull[wb]);
       const bool period_end = (it % flush) == flush - 1 || it == my_tiles - 1;
+      // the FP32 sum of w over the period joins the compensated total at the period's last
+      // tile, a fixed point (the Y fold below happens whenever MMA2 is done, which varies), so
+      // the result is the same bit for bit from run to run
+      if (period_end) {
+#pragma unroll
+        for (int c = 0; c < CPG; ++c) {
+          kahan_add(ws[c], wc[c], wacc[c]);
+          wacc[c] = 0.f;
+        }
+      }
       if (period_end && pending >= 0 && !fold(pending, true)) {
         ok = false;
         break;
