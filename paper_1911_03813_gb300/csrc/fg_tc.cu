@@ -254,7 +254,10 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     if (lane == 0) {
       const uint32_t idesc1 = tc::idesc_bf16(128, N, 0, 0);  // V K-major, A split K-major
       const int k1 = (n + 15) / 16;
-      const uint32_t sv0 = tc::smem_addr(sV), sa0 = tc::smem_addr(sA);
+      // shared-memory descriptors are linear in the operand address (16-byte units in the low
+      // bits; every address here is below 256 KB): one base per operand plus (offset >> 4)
+      const uint64_t vdesc0 = tc::sdesc_sw128(tc::smem_addr(sV), 16, 1024);
+      const uint64_t adesc0 = tc::sdesc_sw128(tc::smem_addr(sA), 16, 1024);
       bool ok = true;
       for (int t = 0; t < my_tiles; ++t) {
         const int st = t % S, zb = t & 1;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
              tc::mbar_wait(&zempty[zb], ((t >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
         if (!ok) break;
         tc::tc_fence_after();
-        const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
+        const uint64_t vd = vdesc0 + uint64_t((uint32_t(st) * stage_bytes) >> 4);
         // accumulator c takes K steps [c kpz, min((c + 1) kpz, k1)); one that gets none (small
         // n) takes step c kpz alone, which lies in the zero padding of both operands, so every
         // accumulator is written
@@ -270,13 +273,10 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
           const uint32_t dZ = tmem + uint32_t(zb * ZC + c) * N;
           const int kb = c * kpz;
           const int ke = kb + kpz < k1 ? kb + kpz : (kb < k1 ? k1 : kb + 1);
-          for (int kk = kb; kk < ke; ++kk) {
-            const uint64_t ad =
-                tc::sdesc_sw128(vb + (kk >> 2) * REG_BYTES + (kk & 3) * 32, 16, 1024);
-            const uint64_t bd =
-                tc::sdesc_sw128(sa0 + (kk >> 2) * C::A_REG + (kk & 3) * 32, 16, 1024);
-            tc::mma_bf16(dZ, ad, bd, idesc1, kk > kb ? 1u : 0u);
-          }
+          for (int kk = kb; kk < ke; ++kk)
+            tc::mma_bf16(dZ, vd + uint64_t(((kk >> 2) * REG_BYTES + (kk & 3) * 32) >> 4),
+                         adesc0 + uint64_t(((kk >> 2) * C::A_REG + (kk & 3) * 32) >> 4), idesc1,
+                         kk > kb ? 1u : 0u);
         }
         tc::mma_commit(&zfull[zb]);
       }
@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     // A separate issuing thread keeps this from queueing behind the next tile's MMA1 issue.
     if (lane == 0) {
       const uint32_t idesc2 = tc::idesc_bf16(128, N, 1, 0);  // V^T MN-major, W K-major
-      const uint32_t sv0 = tc::smem_addr(sV), sw0 = tc::smem_addr(sW);
+      const uint64_t vdesc0 = tc::sdesc_sw128(tc::smem_addr(sV), REG_BYTES, 1024);
+      const uint64_t wdesc0 = tc::sdesc_sw128(tc::smem_addr(sW), 16, 1024);
       bool ok = true;
       for (int t = 0; t < my_tiles; ++t) {
         const int st = t % S, wb = t & 1;
@@ -300,17 +301,16 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         ok = ok && tc::mbar_wait(&wfull[wb], (t >> 1) & 1, abortv, WAIT_LIMIT);
         if (!ok) break;
         tc::tc_fence_after();
-        const uint32_t vb = sv0 + uint32_t(st) * stage_bytes;
-        const uint32_t wbb = sw0 + uint32_t(wb) * 2 * C::W_REG;
+        const uint64_t wd = wdesc0 + uint64_t((uint32_t(wb) * 2 * C::W_REG) >> 4);
         for (int mb = 0; mb < nmb; ++mb) {
           const uint32_t dY = tmem + uint32_t(2 * ZC + yb * 2 + mb) * N;
-          for (int kk = 0; kk < TM / 16; ++kk) {
-            const uint64_t ad = tc::sdesc_sw128(vb + uint32_t(2 * mb) * REG_BYTES + kk * 2048,
-                                                REG_BYTES, 1024);
-            const uint64_t bd =
-                tc::sdesc_sw128(wbb + (kk >> 2) * C::W_REG + (kk & 3) * 32, 16, 1024);
-            tc::mma_bf16(dY, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
-          }
+          const uint64_t vd =
+              vdesc0 + uint64_t((uint32_t(st) * stage_bytes + uint32_t(2 * mb) * REG_BYTES) >> 4);
+#pragma unroll
+          for (int kk = 0; kk < TM / 16; ++kk)
+            tc::mma_bf16(dY, vd + uint64_t((kk * 2048) >> 4),
+                         wd + uint64_t(((kk >> 2) * C::W_REG + (kk & 3) * 32) >> 4), idesc2,
+                         (first && kk == 0) ? 0u : 1u);
         }
         tc::mma_commit(&empty[st]);
         tc::mma_commit(&wempty[wb]);
@@ -424,22 +424,29 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       pending = -1;
       return true;
     };
+    // The weight of this thread's sample in tile it (and, for E4M3, its scale) is loaded one
+    // tile ahead, so the loads' latency stays off the per-tile chain.
+    float nu_next = 0.f, sc_next = 1.f;
+    auto load_weight = [&](int it_) {
+      const int64_t sidx_ = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + L;
+      nu_next = 0.f;
+      if (it_ < my_tiles && sidx_ < prm.p) {
+        nu_next = prm.nu ? (float)prm.nu[sidx_] : (float)prm.nu_uniform;
+        if constexpr (FP8) sc_next = prm.scale[sidx_];
+      }
+    };
+    load_weight(0);
     bool ok = true;
     for (int it = 0; it < my_tiles; ++it) {
       const int zb = it & 1, wb = it & 1;
-      const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
-      const int64_t sidx = tile * TM + L;
-      float nu_s = 0.f;
-      if (sidx < prm.p) {
-        double nu_d = prm.nu ? prm.nu[sidx] : prm.nu_uniform;
-        if constexpr (FP8) {  // nu' = nu s^d (the scale of sample l folded into its weight)
-          const double sc = (double)prm.scale[sidx];
-          double sd = sc;
-          for (int e = 1; e < d; ++e) sd *= sc;
-          nu_d *= sd;
-        }
-        nu_s = (float)nu_d;
+      float nu_s = nu_next;
+      if constexpr (FP8) {  // nu' = nu s^d (the scale of sample l folded into its weight), FP32
+        const float sc = sc_next;
+        float sd = sc;
+        for (int e = 1; e < d; ++e) sd *= sc;
+        nu_s *= sd;
       }
+      load_weight(it + 1);
       if (!tc::mbar_wait(&zfull[zb], (it >> 1) & 1, abortv, WAIT_LIMIT)) {
         ok = false;
         break;

@@ -472,12 +472,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       pending = -1;
       return true;
     };
+    // the weight of this thread's sample in tile it is loaded one tile ahead
+    auto weight_of = [&](int it_) -> float {
+      const int64_t sidx_ = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + L;
+      if (it_ >= my_tiles || sidx_ >= prm.p) return 0.f;
+      return prm.nu ? (float)prm.nu[sidx_] : (float)prm.nu_uniform;
+    };
+    float nu_next = weight_of(0);
     bool ok = true;
     for (int it = 0; it < my_tiles; ++it) {
       const int wb = it % WB, zb = it % ZBUF;
-      const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
-      const int64_t sidx = tile * TM + L;
-      const float nu_s = sidx < prm.p ? (float)(prm.nu ? prm.nu[sidx] : prm.nu_uniform) : 0.f;
+      const float nu_s = nu_next;
+      nu_next = weight_of(it + 1);
       if (!tc::mbar_wait_sleep(&zfull[zb], (it / ZBUF) & 1, abortv, WAIT_LIMIT)) {
         ok = false;
         break;
