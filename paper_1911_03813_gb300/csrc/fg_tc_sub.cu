@@ -1,42 +1,48 @@
-// Fused pass over FP32 samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM).
+// Fused pass over samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM), streaming
+// each tile through a ring of sub-stages: FP32 samples (n <= 256), and BF16 or E4M3 samples with
+// more features than the whole-tile pass holds (n <= 512).
 //
-// Computes the same per-CTA partial sums of Alg. 2 as the BF16 pass (Lemma 3.3, eq. Y; Lemma 3.5):
+// Computes the same per-CTA partial sums of Alg. 2 as the whole-tile pass (Lemma 3.3, eq. Y;
+// Lemma 3.5):
 //     Y_part = sum_l nu_l (v_l^T A)^{d-1} v_l,      w_part_j = sum_l nu_l (v_l^T a_j)^d,
-// reading every FP32 sample from HBM exactly once.
+// reading every sample from HBM exactly once. A sub-stage is 32 KB of shared memory: two
+// regions of 128 sample rows x 128 bytes (the 128-byte swizzle) holding BF16 values for MMAs:
+//   FP32  64 features, two TMA boxes of 32 FP32 features; each value x is split in place into
+//         two BF16 terms, b1 = bf16(x) and b2 = bf16(x - b1) (2^-18 relative: x - b1 is exact in
+//         FP32 and b2 keeps its leading 8 bits), region g (features 32g .. 32g + 31) becoming
+//         row by row [b1 of its 32 features | b2 of them]; z = b1 A + b2 A.
+//   BF16  128 features, two TMA boxes of 64 BF16 features, used as they land.
+//   E4M3  128 features, one TMA box of 128 codes landing in region 1 and widened in place into
+//         both regions (every E4M3 value is a BF16 value); the per-sample scale s folds into the
+//         weight, nu' = nu s^d, so z = q^T a with the codes q.
+// Per sub-stage h of a tile:
+//   MMA1  Z += V_h A_split(features of h)        M = 128 samples, N = 3 RP (16-padded)
+//         (FP32: the b2 products N = 2 RP into their own accumulator)
+//   MMA2  Y_h += V_h^T [W_hi, W_lo]               M = 128 rows of the sub-stage, N = 2 RP
+// MMA2's block h reads only sub-stage h and releases it when done, so a tile needs at most four
+// sub-stages at a time and the ring of six keeps the next tile streaming in. A (FP64) is split
+// once per CTA into three BF16 terms A1 + A2 + A3 (2^-25 relative): the split of A is the same
+// perturbation for every sample, so unlike the rounding of W and V it does not average out over
+// samples, and a two-term split (2^-17) would show in the small entries of G_A. W is split per
+// tile into BF16 hi/lo. The tensor cores' FP32 accumulation truncates, so every addition into an
+// accumulator biases |z| low by up to an ulp of the running sum: the products go to two
+// accumulators (even and odd sub-stages) and, for FP32, the b2 products, 2^-8 of the size, to a
+// third, so no accumulator takes more additions than K = 256 split in two.
 //
-// Each FP32 value x is split in shared memory into two BF16 terms, b1 = bf16(x) and
-// b2 = bf16(x - b1), which carry x to 2^-18 relative (x - b1 is exact in FP32; b2 keeps its
-// leading 8 bits). The pair occupies the 4 bytes x came in, so the split is done in place and
-// the pass becomes the BF16 pass over 2n "features": z = [b1 b2] [A; A] and the two halves of
-// V^T W are summed at the end. Tiles of 128 samples arrive as sub-stages of 64 features
-// (32 KB: two TMA boxes, regions, of 32 FP32 features). Per sub-stage h of a tile:
-//   convert  region g (features 32g .. 32g + 31 of the sub-stage) becomes, row by row,
-//            [b1 of its 32 features | b2 of its 32 features] (BF16, 128-byte swizzle)
-//   MMA1     Z_b1 += b1 [A1, A2, A3](features 64h..)       M = 128 samples, N = 3 RP (16-padded)
-//            Z_b2 += b2 [A1, A2]                            N = 2 RP
-//   MMA2     Y_h += [b1 ; b2]^T [W_hi, W_lo]                M = 128 (b1 rows, then b2 rows)
-// MMA2's block h reads only sub-stage h and releases it when done, so a tile of n <= 256
-// features needs at most four 32 KB sub-stages at a time and the ring of six keeps the next tile
-// streaming in. A (FP64) is split once per CTA into three BF16 terms A1 + A2 + A3 (2^-25
-// relative): the split of A is the same perturbation for every sample, so unlike the rounding of
-// W and V it does not average out over samples, and a two-term split (2^-17) would show in the
-// small entries of G_A. W is split per tile into BF16 hi/lo, as in the BF16 pass. The tensor
-// cores' FP32 accumulation truncates, so every addition into an accumulator biases |z| low by
-// up to an ulp of the running sum: the b1 products go to two accumulators (even and odd
-// sub-stages, as the BF16 pass splits K) and the b2 products, 2^-8 of the size, to a third, so
-// no accumulator takes more additions than in the BF16 pass.
-//
-// So each K step of 16 of MMA1 is either all b1 or all b2, and the rows of MMA2 block h are
-// [b1 f0-31; b2 f0-31; b1 f32-63; b2 f32-63] of sub-stage h's features.
+// FP32: each K step of 16 of MMA1 is either all b1 or all b2, and the rows of MMA2 block h are
+// [b1 f0-31; b2 f0-31; b1 f32-63; b2 f32-63] of sub-stage h's features; BF16/E4M3: rows are
+// features 128h .. 128h + 127.
 //
 // Warp roles (736 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
 // warp 2 = MMA2 issuer, warps 3-18 = epilogue (four warpgroups that split the components;
 // thread = TMEM lane = sample of the tile, or row of an MMA2 block), warps 19-22 = converters
-// (thread = one sample row of both regions, so the in-place rewrite never crosses threads).
-// Every wait is bounded: a wait that runs out sets STMF_ETIMEOUT in the status word and all
-// roles wind down, wait for their own copies and MMAs, and free TMEM.
+// (FP32 and E4M3; thread = one sample row of both regions, so the in-place rewrite never
+// crosses threads). Every wait is bounded: a wait that runs out sets STMF_ETIMEOUT in the
+// status word and all roles wind down, wait for their own copies and MMAs, and free TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "stmf_internal.h"
 #include "tc_common.cuh"
@@ -46,8 +52,10 @@ namespace {
 
 constexpr int TM = 128;                  // samples per tile
 constexpr int REG_BYTES = TM * 128;      // one region: 128 rows of 128 bytes (16 KB)
-constexpr int SUB_BYTES = 2 * REG_BYTES; // one sub-stage: 64 FP32 features of 128 samples
-constexpr int MAX_SUB = 4;               // n <= 256
+constexpr int SUB_BYTES = 2 * REG_BYTES; // one sub-stage (two regions)
+constexpr int MAX_SUB = 4;               // sub-stages per tile: n <= 256 (FP32), 512 (BF16, E4M3)
+enum SubMode { kF32 = 0, kBF16 = 1, kE4M3 = 2 };
+__host__ __device__ constexpr int feats_per_sub(int mode) { return mode == kF32 ? 64 : 128; }
 constexpr int EG = 4;                    // epilogue warpgroups
 constexpr int NEPI = 128 * EG;
 constexpr int NCONV = 4;                 // converter warps: one thread per sample row
@@ -55,8 +63,8 @@ constexpr int CONV0 = 96 + NEPI;         // first converter thread
 constexpr int NTHREADS = CONV0 + 32 * NCONV;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
-struct Tc32Extra {
-  int nsub;        // sub-stages per tile: ceil(n / 64)
+struct SubExtra {
+  int nsub;        // sub-stages per tile: ceil(n / features per sub-stage)
   int zbufs;       // Z buffers in TMEM: 2 where they fit beside Y, else 1
   int ring;        // sub-stage slots in shared memory
   int wbufs;       // W buffers: 2, or 1 where a second one would cost a ring slot
@@ -117,20 +125,24 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 }
 
 // z of one warpgroup's CPG components from a Z buffer at `zaddr`: the b2 accumulator's two
-// terms, the second b1 accumulator's three (when there is more than one sub-stage) and the
-// first's three, each accumulator's terms summed smallest first, in FP32 rounded to nearest.
-// ONE_BY_ONE reads the accumulators one at a time (three waits instead of one) so that at most
-// three terms are live: the variant for n > 192 keeps four blocks of Y sums in registers.
-template <int CPG, int RP, int ZS, bool ONE_BY_ONE>
-__device__ __forceinline__ void tmem_z(uint32_t zaddr, bool two_b1, float (&z)[CPG]) {
+// terms (FP32 samples only: HAS_B2), the second accumulator's three (when there is more than one
+// sub-stage) and the first's three, each accumulator's terms summed smallest first, in FP32
+// rounded to nearest. ONE_BY_ONE reads the accumulators one at a time (a wait each) so that at
+// most three terms are live: the variant with four blocks of Y sums in registers needs that.
+template <int CPG, int RP, int ZS, bool ONE_BY_ONE, bool HAS_B2>
+__device__ __forceinline__ void tmem_z(uint32_t zaddr, bool two_acc, float (&z)[CPG]) {
   if constexpr (ONE_BY_ONE) {
     float v[3][CPG];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[k]);
-    tc::tmem_ld_wait();
+    for (int c = 0; c < CPG; ++c) z[c] = 0.f;
+    if constexpr (HAS_B2) {
 #pragma unroll
-    for (int c = 0; c < CPG; ++c) z[c] = v[1][c] + v[0][c];
-    if (two_b1) {
+      for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[k]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int c = 0; c < CPG; ++c) z[c] = v[1][c] + v[0][c];
+    }
+    if (two_acc) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[k]);
       tc::tmem_ld_wait();
@@ -148,17 +160,30 @@ __device__ __forceinline__ void tmem_z(uint32_t zaddr, bool two_b1, float (&z)[C
     for (int k = 0; k < 3; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(k * RP), v[k]);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      if (two_b1) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[3 + k]);
+      if (two_acc) tmem_load_cols<CPG>(zaddr + uint32_t(ZS + k * RP), v[3 + k]);
+    if constexpr (HAS_B2) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[6 + k]);
+      for (int k = 0; k < 2; ++k)
+        tmem_load_cols<CPG>(zaddr + uint32_t(2 * ZS + k * RP), v[6 + k]);
+    }
     tc::tmem_ld_wait();
 #pragma unroll
     for (int c = 0; c < CPG; ++c) {
-      float t = v[7][c] + v[6][c];
-      if (two_b1) t += (v[5][c] + v[4][c]) + v[3][c];
+      float t = 0.f;
+      if constexpr (HAS_B2) t = v[7][c] + v[6][c];
+      if (two_acc) t += (v[5][c] + v[4][c]) + v[3][c];
       z[c] = t + ((v[2][c] + v[1][c]) + v[0][c]);
     }
   }
+}
+
+// Two E4M3 codes -> two BF16 values, exactly (E4M3 -> FP16 -> FP32 -> BF16; every E4M3 value
+// has at most 4 significant bits and an exponent in -9..8, so no step rounds).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint16_t q) {
+  const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)q, __NV_E4M3);
+  const __half2 hh = *reinterpret_cast<const __half2*>(&hr);
+  const __nv_bfloat162 bb = __floats2bfloat162_rn(__low2float(hh), __high2float(hh));
+  return *reinterpret_cast<const uint32_t*>(&bb);
 }
 
 // Eight FP32 values -> their BF16 leading terms (b1) and BF16 remainders (b2), packed in pairs.
@@ -183,9 +208,14 @@ __device__ __forceinline__ void epi_barrier() {
 }
 
 // NS: sub-stages per tile the epilogue keeps Y sums for (1, 2 or 4; at least ex.nsub).
-template <int RP, int NS>
+// MODE: the storage type of the samples (SubMode).
+template <int RP, int NS, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    fg_tc32_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const Tc32Extra ex) {
+    fg_tc_sub_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm,
+                     const SubExtra ex) {
+  constexpr int FS = feats_per_sub(MODE);  // features per sub-stage
+  constexpr int AR = FS / 64;              // A-split regions per sub-stage
+  constexpr bool CONVERT = MODE != kBF16;  // converter warps rewrite each sub-stage
   using C = Cfg32<RP>;
   constexpr int N1 = C::N1;
   constexpr int N2 = C::N2;
@@ -202,10 +232,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int n = prm.n, r = prm.r, d = prm.d;
   unsigned char* sV = base;                              // ring of R sub-stages
   unsigned char* sW = sV + size_t(R) * SUB_BYTES;        // WB buffers x 2 regions
-  unsigned char* sA = sW + size_t(WB) * 2 * C::W_REG;    // nsub regions
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nsub) * C::A_REG);
+  unsigned char* sA = sW + size_t(WB) * 2 * C::W_REG;    // nsub x AR regions
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nsub * AR) * C::A_REG);
   uint64_t* full = bars;            // [R] TMA landed
-  uint64_t* conv = bars + R;        // [R] split into BF16 terms
+  uint64_t* conv = bars + R;        // [R] rewritten as BF16 (FP32, E4M3)
   uint64_t* empty = bars + 2 * R;   // [R] MMA2 done with the sub-stage
   uint64_t* zfull = bars + 3 * R;  // [ZBUF]
   uint64_t* zempty = zfull + 2;
@@ -243,10 +273,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
 
   // A split: row k RP + j holds term k of a_j, with A1 = BF16(a), A2 = BF16(a - A1),
-  // A3 = BF16(a - A1 - A2) (rows past 3 RP are zero); the same region h serves the b1 and the b2
-  // half of sub-stage h
+  // A3 = BF16(a - A1 - A2) (rows past 3 RP are zero), in regions of 64 features (FP32: region h
+  // serves the b1 and the b2 half of sub-stage h)
   {
-    const int kext = nsub * 64;
+    const int kext = nsub * FS;
     for (int e = tid; e < N1 * kext; e += NTHREADS) {
       const int row = e / kext, k = e - row * kext;
       const int term = row / RP, j = row % RP;
@@ -288,10 +318,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = false;
             break;
           }
-          tc::mbar_arrive_expect_tx(&full[slot], SUB_BYTES);
           unsigned char* dst = sV + size_t(slot) * SUB_BYTES;
-          tc::tma_load_2d(dst, &tmap, 64 * h, (int32_t)(tile * TM), &full[slot]);
-          tc::tma_load_2d(dst + REG_BYTES, &tmap, 64 * h + 32, (int32_t)(tile * TM), &full[slot]);
+          const int32_t y0 = (int32_t)(tile * TM);
+          if constexpr (MODE == kE4M3) {  // 128 codes per row, into region 1
+            tc::mbar_arrive_expect_tx(&full[slot], REG_BYTES);
+            tc::tma_load_2d(dst + REG_BYTES, &tmap, FS * h, y0, &full[slot]);
+          } else {  // two boxes of FS / 2 features (128-byte rows)
+            tc::mbar_arrive_expect_tx(&full[slot], SUB_BYTES);
+            tc::tma_load_2d(dst, &tmap, FS * h, y0, &full[slot]);
+            tc::tma_load_2d(dst + REG_BYTES, &tmap, FS * h + FS / 2, y0, &full[slot]);
+          }
           ++issued;
         }
       }
@@ -319,24 +355,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t written = 0;
         for (int h = 0; h < nsub && ok; ++h, ++seq) {
           const int slot = seq % R;
-          ok = tc::mbar_wait_sleep(&conv[slot], (seq / R) & 1, abortv, WAIT_LIMIT);
+          ok = tc::mbar_wait_sleep(CONVERT ? &conv[slot] : &full[slot], (seq / R) & 1, abortv,
+                                   WAIT_LIMIT);
           if (!ok) break;
           tc::tc_fence_after();
           const uint64_t vd = vdesc0 + uint64_t((uint32_t(slot) * SUB_BYTES) >> 4);
-          const uint64_t ad0 = adesc0 + uint64_t((uint32_t(h) * C::A_REG) >> 4);
-          // K step kk of region g: kk = 0, 1 are b1, kk = 2, 3 b2, of features 32g + 16 (kk % 2)
+          const uint64_t ad0 = adesc0 + uint64_t((uint32_t(h * AR) * C::A_REG) >> 4);
+          if constexpr (MODE == kF32) {
+            // K step kk of region g: kk = 0, 1 are b1, kk = 2, 3 b2, of features 32g + 16 (kk % 2)
 #pragma unroll
-          for (int part = 0; part < 2; ++part) {
-            const int acc = part == 0 ? (h & 1) : 2;
+            for (int part = 0; part < 2; ++part) {
+              const int acc = part == 0 ? (h & 1) : 2;
+              const uint32_t dZ = tmem + uint32_t(zb * C::ZBS + acc * ZS);
+              const uint32_t idesc = part == 0 ? idesc_b1 : idesc_b2;
+              const uint32_t first = (written >> acc) & 1u;
+#pragma unroll
+              for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk)
+                  tc::mma_bf16(dZ, vd + uint64_t((g * REG_BYTES + (2 * part + kk) * 32) >> 4),
+                               ad0 + uint64_t(((2 * g + kk) * 32) >> 4), idesc,
+                               (g | kk) ? 1u : first);
+              written |= 1u << acc;
+            }
+          } else {
+            // region g holds features 64g .. 64g + 63 of the sub-stage, A-split region 2h + g
+            const int acc = h & 1;
             const uint32_t dZ = tmem + uint32_t(zb * C::ZBS + acc * ZS);
-            const uint32_t idesc = part == 0 ? idesc_b1 : idesc_b2;
             const uint32_t first = (written >> acc) & 1u;
 #pragma unroll
             for (int g = 0; g < 2; ++g)
 #pragma unroll
-              for (int kk = 0; kk < 2; ++kk)
-                tc::mma_bf16(dZ, vd + uint64_t((g * REG_BYTES + (2 * part + kk) * 32) >> 4),
-                             ad0 + uint64_t(((2 * g + kk) * 32) >> 4), idesc,
+              for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(dZ, vd + uint64_t((g * REG_BYTES + kk * 32) >> 4),
+                             ad0 + uint64_t((g * C::A_REG + kk * 32) >> 4), idesc_b1,
                              (g | kk) ? 1u : first);
             written |= 1u << acc;
           }
@@ -386,48 +438,77 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_wait_sleep(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
     }
   } else if (tid >= CONV0) {
-    // ------------------------------------------------------------------ FP32 -> BF16 b1 | b2
-    // Thread y owns row y (sample y of the tile) of both regions of every sub-stage. Per region
-    // it reads the 32 FP32 values of its row (16-byte chunk c of row y at chunk position
-    // c ^ (y & 7)), then writes b1 of the 32 features as BF16 chunks 0-3 and b2 as chunks 4-7 of
-    // the same row, in the same swizzle. Only this thread touches the row, so nothing else reads
-    // the bytes it overwrites.
-    const int y = tid - CONV0;
-    const uint32_t sw = uint32_t(y & 7);
-    bool ok = true;
-    int seq = 0;
-    for (int it = 0; it < my_tiles && ok; ++it) {
-      for (int h = 0; h < nsub; ++h, ++seq) {
-        const int slot = seq % R;
-        if (!tc::mbar_wait_sleep(&full[slot], (seq / R) & 1, abortv, WAIT_LIMIT)) {
-          ok = false;
-          break;
-        }
+    // ------------------------------------------------------------------ converters
+    // Thread y owns row y (sample y of the tile) of both regions of every sub-stage; only this
+    // thread touches the row, so nothing else reads the bytes it overwrites (16-byte chunk c of
+    // row y sits at chunk position c ^ (y & 7) in either layout).
+    // FP32: per region, the 32 FP32 values of the row become b1 of the 32 features (BF16 chunks
+    //       0-3) and b2 (chunks 4-7).
+    // E4M3: the 128 codes of the row (region 1) become the BF16 values of features 0-63 (region
+    //       0) and 64-127 (region 1); all codes are read before anything is written.
+    if constexpr (CONVERT) {
+      const int y = tid - CONV0;
+      const uint32_t sw = uint32_t(y & 7);
+      bool ok = true;
+      int seq = 0;
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        for (int h = 0; h < nsub; ++h, ++seq) {
+          const int slot = seq % R;
+          if (!tc::mbar_wait_sleep(&full[slot], (seq / R) & 1, abortv, WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          unsigned char* row0 = sV + size_t(slot) * SUB_BYTES + y * 128;
+          if constexpr (MODE == kF32) {
 #pragma unroll 1
-        for (int rg = 0; rg < 2; ++rg) {
-        unsigned char* row = sV + size_t(slot) * SUB_BYTES + size_t(rg) * REG_BYTES + y * 128;
-        float x[8][4];
+            for (int rg = 0; rg < 2; ++rg) {
+              unsigned char* row = row0 + size_t(rg) * REG_BYTES;
+              float x[8][4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 a = *reinterpret_cast<const float4*>(row + ((c ^ sw) << 4));
-          x[c][0] = a.x; x[c][1] = a.y; x[c][2] = a.z; x[c][3] = a.w;
-        }
+              for (int c = 0; c < 8; ++c) {
+                const float4 a = *reinterpret_cast<const float4*>(row + ((c ^ sw) << 4));
+                x[c][0] = a.x; x[c][1] = a.y; x[c][2] = a.z; x[c][3] = a.w;
+              }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {  // features 8k .. 8k + 7 of the region
-          const float v[8] = {x[2 * k][0],     x[2 * k][1],     x[2 * k][2],     x[2 * k][3],
-                              x[2 * k + 1][0], x[2 * k + 1][1], x[2 * k + 1][2], x[2 * k + 1][3]};
-          uint4 hi, lo;
-          split8(v, hi, lo);
-          *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
-          *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
+              for (int k = 0; k < 4; ++k) {  // features 8k .. 8k + 7 of the region
+                const float v[8] = {x[2 * k][0],     x[2 * k][1],     x[2 * k][2],
+                                    x[2 * k][3],     x[2 * k + 1][0], x[2 * k + 1][1],
+                                    x[2 * k + 1][2], x[2 * k + 1][3]};
+                uint4 hi, lo;
+                split8(v, hi, lo);
+                *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
+                *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
+              }
+            }
+          } else {
+            unsigned char* row1 = row0 + REG_BYTES;
+            uint4 raw[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              raw[c] = *reinterpret_cast<const uint4*>(row1 + ((uint32_t(c) ^ sw) << 4));
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {  // codes 16c .. 16c + 15 -> BF16 chunks 2c, 2c + 1
+              unsigned char* dst = (c < 4) ? row0 : row1;
+              const uint32_t k0 = uint32_t(2 * (c & 3));
+              const uint32_t w[4] = {raw[c].x, raw[c].y, raw[c].z, raw[c].w};
+              uint32_t o[8];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                o[2 * k] = e4m3x2_to_bf16x2((uint16_t)(w[k] & 0xFFFFu));
+                o[2 * k + 1] = e4m3x2_to_bf16x2((uint16_t)(w[k] >> 16));
+              }
+              *reinterpret_cast<uint4*>(dst + ((k0 ^ sw) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+              *reinterpret_cast<uint4*>(dst + (((k0 + 1) ^ sw) << 4)) =
+                  make_uint4(o[4], o[5], o[6], o[7]);
+            }
+          }
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&conv[slot]);
         }
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&conv[slot]);
       }
+      if (!ok) fail();
     }
-    if (!ok) fail();
   } else {
     // ------------------------------------------------------------------ epilogue
     const int g = (warp - 3) >> 2;
@@ -472,17 +553,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       pending = -1;
       return true;
     };
-    // the weight of this thread's sample in tile it is loaded one tile ahead
+    // The weight of this thread's sample in tile it (and, for E4M3, its scale) is loaded one
+    // tile ahead, so the loads' latency stays off the per-tile chain.
+    float sc_next = 1.f;
     auto weight_of = [&](int it_) -> float {
       const int64_t sidx_ = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + L;
       if (it_ >= my_tiles || sidx_ >= prm.p) return 0.f;
+      if constexpr (MODE == kE4M3) sc_next = prm.scale[sidx_];
       return prm.nu ? (float)prm.nu[sidx_] : (float)prm.nu_uniform;
     };
     float nu_next = weight_of(0);
     bool ok = true;
     for (int it = 0; it < my_tiles; ++it) {
       const int wb = it % WB, zb = it % ZBUF;
-      const float nu_s = nu_next;
+      float nu_s = nu_next;
+      if constexpr (MODE == kE4M3) {  // nu' = nu s^d: the sample's scale folded into its weight
+        const float sc = sc_next;
+        float sd = sc;
+        for (int e = 1; e < d; ++e) sd *= sc;
+        nu_s *= sd;
+      }
       nu_next = weight_of(it + 1);
       if (!tc::mbar_wait_sleep(&zfull[zb], (it / ZBUF) & 1, abortv, WAIT_LIMIT)) {
         ok = false;
@@ -490,7 +580,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc::tc_fence_after();
       float zsum[CPG];
-      tmem_z<CPG, RP, ZS, (NS > 2)>(tmem + uint32_t(zb * C::ZBS + j0) + lane_off, nsub > 1, zsum);
+      tmem_z<CPG, RP, ZS, (NS > 2), MODE == kF32>(tmem + uint32_t(zb * C::ZBS + j0) + lane_off,
+                                                  nsub > 1, zsum);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&zempty[zb]);
@@ -541,14 +632,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    // Lane quarter q of MMA2 block h holds part q % 2 (b1, b2) of features
+    // FP32: lane quarter q of MMA2 block h holds part q % 2 (b1, b2) of features
     // 64h + 32 (q / 2) + lane: the b2 quarters pass their sums to the b1 quarters of the same
     // warpgroup through shared memory (the ring is idle by now: every copy has landed and every
     // MMA has completed once the last fold is done). Every epilogue thread reaches the barrier,
-    // also after a failed wait.
-    const int fi = 32 * (q >> 1) + lane;  // feature within the sub-stage
+    // also after a failed wait. BF16 / E4M3: lane L of block h holds feature FS h + L.
+    const int fi = MODE == kF32 ? 32 * (q >> 1) + lane : L;  // feature within the sub-stage
+    const bool writer = MODE == kF32 ? !(q & 1) : true;
     double* xch = reinterpret_cast<double*>(sV);  // [NS][64][RP]
-    if (ok && (q & 1)) {
+    if (MODE == kF32 && ok && (q & 1)) {
 #pragma unroll
       for (int h = 0; h < NS; ++h)
         if (h < nsub) {
@@ -567,15 +659,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       double corr[CPG];
 #pragma unroll
       for (int c = 0; c < CPG; ++c) corr[c] = 0.0;
-      if (!(q & 1)) {
+      if (writer) {
 #pragma unroll
         for (int h = 0; h < NS; ++h) {
-          const int i = 64 * h + fi;
+          const int i = FS * h + fi;
           if (h < nsub && i < n) {
 #pragma unroll
             for (int c = 0; c < CPG; ++c)
               if (j0 + c < r) {
-                const double y = ((double)ys[h][c] - (double)yc[h][c]) + xch[(h * 64 + fi) * RP + j0 + c];
+                const double y = ((double)ys[h][c] - (double)yc[h][c]) +
+                                 (MODE == kF32 ? xch[(h * 64 + fi) * RP + j0 + c] : 0.0);
                 part[r + i + size_t(n) * (j0 + c)] = y;
                 const double a = prm.A[i + size_t(n) * (j0 + c)];
                 const double a1 = (double)__bfloat162float(__double2bfloat16(a));
@@ -611,7 +704,7 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-EncodeFn get_encode32() {
+EncodeFn get_encode_sub() {
   static EncodeFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -626,16 +719,22 @@ EncodeFn get_encode32() {
 
 int rp_of(int r) { return r <= 8 ? 8 : 16; }
 
-Tc32Extra plan32(int n, int r) {
-  Tc32Extra ex{};
-  ex.nsub = (n + 63) / 64;
+int mode_of(int dtype) {
+  return dtype == STMF_F32 ? kF32 : dtype == STMF_BF16 ? kBF16 : dtype == STMF_E4M3 ? kE4M3 : -1;
+}
+
+SubExtra plan_sub(int mode, int n, int r) {
+  SubExtra ex{};
+  const int fs = feats_per_sub(mode);
+  ex.nsub = (n + fs - 1) / fs;
   const int RP = rp_of(r), N1 = (3 * RP + 15) / 16 * 16, N2 = 2 * RP;
+  const int a_bytes = ex.nsub * (fs / 64) * N1 * 128;
   // W buffers, A split, 1024 bytes of alignment slack and 1024 of barriers and w sums; a
   // second W buffer lets the epilogue write W(t+1) while MMA2 still reads W(t), but a deeper
-  // ring matters more: keep six sub-stage slots when the A split of n > 192 needs the room
+  // ring matters more: keep six sub-stage slots when the A split of many features needs the room
   int fixed = 0, R = 0;
   for (ex.wbufs = 2; ex.wbufs >= 1; --ex.wbufs) {
-    fixed = ex.wbufs * 2 * N2 * 128 + ex.nsub * N1 * 128 + 1024 + 1024;
+    fixed = ex.wbufs * 2 * N2 * 128 + a_bytes + 1024 + 1024;
     R = (int(kMaxSmem) - fixed) / SUB_BYTES;
     if (R >= 6) break;
   }
@@ -653,55 +752,70 @@ Tc32Extra plan32(int n, int r) {
   return ex;
 }
 
-template <int RP, int NS>
-cudaError_t launch32(const CUtensorMap& tmap, const FgParams& prm, const Tc32Extra& ex, int grid,
-                     cudaStream_t s) {
-  const cudaError_t e = smem_limit((const void*)fg_tc32_kernel<RP, NS>, (int)kMaxSmem);
+template <int RP, int NS, int MODE>
+cudaError_t launch_sub(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex, int grid,
+                       cudaStream_t s) {
+  const cudaError_t e = smem_limit((const void*)fg_tc_sub_kernel<RP, NS, MODE>, (int)kMaxSmem);
   if (e != cudaSuccess) return e;
-  return launch_kernel(fg_tc32_kernel<RP, NS>, dim3(grid), dim3(NTHREADS), size_t(ex.smem_bytes),
-                       s, tmap, prm, ex);
+  return launch_kernel(fg_tc_sub_kernel<RP, NS, MODE>, dim3(grid), dim3(NTHREADS),
+                       size_t(ex.smem_bytes), s, tmap, prm, ex);
 }
 
-template <int RP>
-cudaError_t launch32_ns(const CUtensorMap& tmap, const FgParams& prm, const Tc32Extra& ex,
-                        int grid, cudaStream_t s) {
-  if (ex.nsub == 1) return launch32<RP, 1>(tmap, prm, ex, grid, s);
-  if (ex.nsub == 2) return launch32<RP, 2>(tmap, prm, ex, grid, s);
-  return launch32<RP, 4>(tmap, prm, ex, grid, s);
+template <int RP, int MODE>
+cudaError_t launch_sub_ns(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex,
+                          int grid, cudaStream_t s) {
+  if (ex.nsub == 1) return launch_sub<RP, 1, MODE>(tmap, prm, ex, grid, s);
+  if (ex.nsub == 2) return launch_sub<RP, 2, MODE>(tmap, prm, ex, grid, s);
+  return launch_sub<RP, 4, MODE>(tmap, prm, ex, grid, s);
+}
+
+template <int MODE>
+cudaError_t launch_sub_rp(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex,
+                          int grid, cudaStream_t s) {
+  if (rp_of(prm.r) == 8) return launch_sub_ns<8, MODE>(tmap, prm, ex, grid, s);
+  return launch_sub_ns<16, MODE>(tmap, prm, ex, grid, s);
 }
 
 }  // namespace
 
-bool fg_tc32_supported(int dtype, int n, int r) {
-  if (dtype != STMF_F32) return false;
-  if (r < 1 || r > 16 || n < 1 || n > 64 * MAX_SUB) return false;
-  if (!get_encode32()) return false;
-  const Tc32Extra ex = plan32(n, r);
-  // the exchange at the end of the epilogue reuses the ring: MAX_SUB x 64 x 16 doubles
+bool fg_tc_sub_supported(int dtype, int n, int r) {
+  const int mode = mode_of(dtype);
+  if (mode < 0) return false;
+  if (r < 1 || r > 16 || n < 1 || n > feats_per_sub(mode) * MAX_SUB) return false;
+  if (!get_encode_sub()) return false;
+  const SubExtra ex = plan_sub(mode, n, r);
+  // the exchange at the end of the FP32 epilogue reuses the ring: MAX_SUB x 64 x 16 doubles
   return ex.ring >= ex.nsub && ex.ring * SUB_BYTES >= MAX_SUB * 64 * 16 * 8;
 }
 
-int fg_tc32_grid(int64_t p, int num_sms) {
+int fg_tc_sub_grid(int64_t p, int num_sms) {
   const int64_t tiles = (p + TM - 1) / TM;
   return (int)(tiles < num_sms ? tiles : num_sms);
 }
 
-cudaError_t fg_tc32_launch(const FgParams& prm, int grid, cudaStream_t s) {
+cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  const int mode = mode_of(dtype);
+  if (mode < 0) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
-  EncodeFn enc = get_encode32();
+  EncodeFn enc = get_encode_sub();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmap;
+  const int eb = mode == kF32 ? 4 : mode == kBF16 ? 2 : 1;
   const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
-  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * 4};
-  const cuuint32_t box[2] = {32u, TM};  // 32 FP32 = 128-byte rows
+  const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * eb};
+  const cuuint32_t box[2] = {128u / eb, TM};  // 128-byte rows
   const cuuint32_t estr[2] = {1, 1};
-  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(prm.V), dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUtensorMapDataType dt = mode == kF32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : mode == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult cr = enc(&tmap, dt, 2, const_cast<void*>(prm.V), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const Tc32Extra ex = plan32(prm.n, prm.r);
-  if (rp_of(prm.r) == 8) return launch32_ns<8>(tmap, prm, ex, grid, s);
-  return launch32_ns<16>(tmap, prm, ex, grid, s);
+  const SubExtra ex = plan_sub(mode, prm.n, prm.r);
+  if (mode == kF32) return launch_sub_rp<kF32>(tmap, prm, ex, grid, s);
+  if (mode == kBF16) return launch_sub_rp<kBF16>(tmap, prm, ex, grid, s);
+  return launch_sub_rp<kE4M3>(tmap, prm, ex, grid, s);
 }
 
 }  // namespace stmf

@@ -97,8 +97,8 @@ bool stmf::plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gathe
   PassPlan pl{kPassSimt, 0};
   if (!gather && fg_tc_supported(dtype, n, r)) {
     pl = {kPassTc, fg_tc_grid(dtype, n, r, p, num_sms)};
-  } else if (!gather && fg_tc32_supported(dtype, n, r)) {
-    pl = {kPassTc32, fg_tc32_grid(p, num_sms)};
+  } else if (!gather && fg_tc_sub_supported(dtype, n, r)) {
+    pl = {kPassTcSub, fg_tc_sub_grid(p, num_sms)};
   } else if (fg_f32_supported(dtype, n, r)) {
     pl = {kPassF32, fg_f32_grid(n, p, num_sms)};
   } else {
@@ -112,7 +112,7 @@ cudaError_t stmf::launch_pass(const stmf::PassPlan& pl, int dtype, const stmf::F
                               cudaStream_t s) {
   switch (pl.kind) {
     case kPassTc: return fg_tc_launch(dtype, prm, pl.grid, s);
-    case kPassTc32: return fg_tc32_launch(prm, pl.grid, s);
+    case kPassTcSub: return fg_tc_sub_launch(dtype, prm, pl.grid, s);
     case kPassF32: return fg_f32_launch(prm, pl.grid, s);
     default: return fg_simt_launch(dtype, prm, pl.grid, s);
   }

@@ -109,10 +109,11 @@ cudaError_t finish_launch(const ModelParams& prm, cudaStream_t s);
 bool fg_f32_supported(int dtype, int n, int r);
 int fg_f32_grid(int n, int64_t p, int num_sms);
 cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s);
-// Tensor-core pass for FP32 samples (each split into two BF16 terms; n <= 256, r <= 16).
-bool fg_tc32_supported(int dtype, int n, int r);
-int fg_tc32_grid(int64_t p, int num_sms);
-cudaError_t fg_tc32_launch(const FgParams& prm, int grid, cudaStream_t s);
+// Tensor-core pass that streams tiles as sub-stages (fg_tc_sub.cu): FP32 samples (each split
+// into two BF16 terms; n <= 256) and BF16 / E4M3 samples with n <= 512; r <= 16.
+bool fg_tc_sub_supported(int dtype, int n, int r);
+int fg_tc_sub_grid(int64_t p, int num_sms);
+cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
@@ -133,10 +134,11 @@ size_t norm_sym_slab_bytes(long long count, dim3 grid);
 int norm_sym_square_blocks(long long count);
 cudaError_t norm_sym_launch(int dtype, const SymParams& prm, dim3 grid, cudaStream_t s);
 
-// The fused pass that serves a request: the tensor-core passes (BF16/E4M3, FP32) for n <= 256
-// and r <= 16, else the register-blocked FP32 pass (FP32, r <= 16), else the CUDA-core pass.
-// Gathered rows (an index array) take the CUDA-core passes only.
-enum PassKind { kPassTc = 0, kPassTc32 = 1, kPassF32 = 2, kPassSimt = 3 };
+// The fused pass that serves a request (r <= 16 for every tensor-core pass): the whole-tile
+// tensor-core pass for BF16/E4M3 with n <= 256, the sub-stage tensor-core pass for FP32 with
+// n <= 256 and for BF16/E4M3 with n <= 512, else the register-blocked FP32 pass (FP32, r <= 16),
+// else the CUDA-core pass. Gathered rows (an index array) take the CUDA-core passes only.
+enum PassKind { kPassTc = 0, kPassTcSub = 1, kPassF32 = 2, kPassSimt = 3 };
 struct PassPlan {
   PassKind kind;
   int grid;

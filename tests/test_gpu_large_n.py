@@ -1,11 +1,13 @@
 """Samples with up to 512 features (-m gpu): the Gaussian-mixture study of Sec. 4.2 fixes n = 500.
 
-Shapes past the tensor-core passes (n > 256) run on the CUDA cores: 64-sample tiles (32 for FP64
-samples, whose 64-sample tile does not fit in shared memory), the Gram pass staged in feature
-chunks, and the range finder in FP32 when its FP64 tile does not fit. The CUDA-core pass
-multiplies decoded BF16/E4M3 values in FP32, so every storage type but FP64 is held to the FP32
-tolerance, 1e-5 normwise and entry by entry with a floor of 0.01 of the largest entry; the FP32
-range finder is compared at 1e-5.
+BF16 and E4M3 samples with 256 < n <= 512 (r <= 16) take the sub-stage tensor-core pass
+(128-feature sub-stages); FP32 and FP64 samples past n = 256 run on the CUDA cores: 64-sample
+tiles (32 for FP64 samples, whose 64-sample tile does not fit in shared memory); the Gram pass is
+staged in feature chunks, and the range finder runs in FP32 when its FP64 tile does not fit.
+Tolerances: FP64 1e-12; FP32 (FP32 arithmetic) 1e-5 normwise and entry by entry with a floor of
+0.01 of the largest entry; BF16/E4M3 on the tensor cores 5e-6 normwise and 1e-5 entry by entry
+with a floor of 0.1 of the largest entry (as for the whole-tile pass); the FP32 range finder is
+compared at 1e-5.
 """
 
 import numpy as np
@@ -20,7 +22,8 @@ from paper_1911_03813_gb300 import inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5, "e4m3": 1e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 5e-6, "e4m3": 5e-6}
+TOL_EL = {"f64": (1e-12, 0.01), "f32": (1e-5, 0.01), "bf16": (1e-5, 0.1), "e4m3": (1e-5, 0.1)}
 
 
 @pytest.fixture(scope="module")
@@ -62,6 +65,11 @@ def dev_model(lam, A):
     ("f32", 512, 5000, 32, 4), ("bf16", 300, 7001, 5, 4),
     ("f64", 500, 3001, 12, 3),   # 32-sample FP64 tiles
     ("f64", 300, 7001, 4, 4),
+    # the sub-stage tensor-core pass: both sides of each 128-feature boundary, r on both sides
+    # of 8, the largest n, ragged tails and enough tiles per block for the ring to wrap
+    ("bf16", 257, 300001, 16, 3), ("e4m3", 257, 30001, 8, 4), ("bf16", 384, 100003, 12, 4),
+    ("e4m3", 385, 50001, 16, 3), ("bf16", 512, 200001, 16, 4), ("e4m3", 512, 70001, 9, 4),
+    ("bf16", 500, 1000, 20, 3),  # r > 16: the CUDA-core pass
 ])
 def test_fg_parity_large_n(stmf, dtype, n, p, r, d):
     data = inputs.gmm(n, p, 5, 0.1, seed=n + p, means="congruent")
@@ -73,12 +81,13 @@ def test_fg_parity_large_n(stmf, dtype, n, p, r, d):
     torch.cuda.synchronize()
     assert stmf.default_context().device_status() == 0
     S = abs(parts["u"] @ lam) + 2 * abs(parts["w"] @ lam)
-    tol = TOL[dtype]
+    tol = TOL[dtype] if r <= 16 else max(TOL[dtype], 1e-5)
     assert abs(f.item() - f_ref) <= tol * S
     assert rel(gl.cpu().numpy(), gl_ref) <= tol
     assert rel(GA.cpu().numpy(), GA_ref) <= tol
-    assert elementwise(gl.cpu().numpy(), gl_ref, 0.01) <= tol
-    assert elementwise(GA.cpu().numpy(), GA_ref, 0.01) <= tol
+    tol_el, c = TOL_EL[dtype] if r <= 16 else (1e-5, 0.01)
+    assert elementwise(gl.cpu().numpy(), gl_ref, c) <= tol_el
+    assert elementwise(GA.cpu().numpy(), GA_ref, c) <= tol_el
 
 
 @pytest.mark.parametrize("dtype,n,r", [("f64", 512, 32), ("f32", 512, 64)])
