@@ -211,6 +211,19 @@ STMF_API stmf_status stmf_norm_x_method(stmf_ctx_t ctx, const stmf_samples* V, c
                                         stmf_stream_t stream);
 
 /*
+ * stmf_set_pass_tiles -- launch shape of this context's tensor-core passes (not part of the
+ * method): each CTA takes at least `min_tiles` tiles of 128 samples, so a pass over p samples
+ * runs on min(#SMs, ceil(p / (128 min_tiles))) CTAs. A CTA of these passes holds a whole SM (its
+ * shared memory): the default, 1, spreads every pass over all SMs, which is fastest for one
+ * evaluation at a time; code that runs many small evaluations at once on other streams (the
+ * server's fit slots use STMF_SERVER_PASS_TILES) gets more of them onto the GPU together with a
+ * larger value. The grouping of per-CTA partial sums depends on the launch shape, so two contexts
+ * give bit-identical results only with the same setting. STMF_EINVAL outside [1, 2^20].
+ */
+#define STMF_SERVER_PASS_TILES 128
+STMF_API stmf_status stmf_set_pass_tiles(stmf_ctx_t ctx, int32_t min_tiles);
+
+/*
  * Kernel timing for benchmarks (not part of the method). While enabled, every stmf_fg records
  * a pair of CUDA events around its fused pass over V, on the call's stream. stmf_profile_read
  * waits for the recorded events, returns the summed pass time in milliseconds and the number of
@@ -280,7 +293,9 @@ STMF_API stmf_status stmf_fit(stmf_ctx_t ctx, const stmf_samples* V, const doubl
  * slots are free and their device footprint fits the memory budget; fits of different requests
  * run at the same time on their own streams, so work that arrives while others run overlaps with
  * them on the GPU. Each fit's kernels use a fixed launch shape and fixed-order reductions, so a
- * result does not depend on what else is running.
+ * result does not depend on what else is running. The slots' contexts take
+ * STMF_SERVER_PASS_TILES tiles per CTA (stmf_set_pass_tiles), so that passes of many small fits
+ * share the GPU.
  * ------------------------------------------------------------------------------------------ */
 typedef struct stmf_server* stmf_server_t;
 

@@ -788,9 +788,14 @@ bool fg_tc_sub_supported(int dtype, int n, int r) {
   return ex.ring >= ex.nsub && ex.ring * SUB_BYTES >= MAX_SUB * 64 * 16 * 8;
 }
 
-int fg_tc_sub_grid(int64_t p, int num_sms) {
+int fg_tc_sub_grid(int64_t p, int num_sms, int min_tiles) {
+  // one CTA per SM, or fewer so that each takes at least min_tiles tiles (a CTA holds a whole SM
+  // through its shared memory, so a small pass spread over every SM keeps concurrent passes off
+  // the GPU while it runs one or two tiles per SM)
   const int64_t tiles = (p + TM - 1) / TM;
-  return (int)(tiles < num_sms ? tiles : num_sms);
+  const int64_t mt = min_tiles > 1 ? min_tiles : 1;
+  const int64_t want = (tiles + mt - 1) / mt;
+  return (int)(want < num_sms ? want : num_sms);
 }
 
 cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {

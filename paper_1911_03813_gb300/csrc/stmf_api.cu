@@ -63,7 +63,8 @@ struct FgPlan {
 
 FgPlan plan_fg(const stmf_ctx* c, const stmf_samples* V, int64_t r, bool gather = false) {
   FgPlan pl;
-  pl.fits = stmf::plan_pass(V->dtype, (int)V->n, (int)r, V->p, c->num_sms, gather, &pl.pass);
+  pl.fits = stmf::plan_pass(V->dtype, (int)V->n, (int)r, V->p, c->num_sms, gather, &pl.pass,
+                            c->min_tiles);
   pl.L = size_t(r) + size_t(V->n) * size_t(r);
   pl.partial_doubles = size_t(pl.pass.grid) * pl.L;
   return pl;
@@ -93,12 +94,12 @@ cudaError_t stmf::smem_limit(const void* kernel, int bytes) {
 }
 
 bool stmf::plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather,
-                     stmf::PassPlan* out) {
+                     stmf::PassPlan* out, int min_tiles) {
   PassPlan pl{kPassSimt, 0};
   if (!gather && fg_tc_supported(dtype, n, r)) {
-    pl = {kPassTc, fg_tc_grid(dtype, n, r, p, num_sms)};
+    pl = {kPassTc, fg_tc_grid(dtype, n, r, p, num_sms, min_tiles)};
   } else if (!gather && fg_tc_sub_supported(dtype, n, r)) {
-    pl = {kPassTcSub, fg_tc_sub_grid(p, num_sms)};
+    pl = {kPassTcSub, fg_tc_sub_grid(p, num_sms, min_tiles)};
   } else if (fg_f32_supported(dtype, n, r)) {
     pl = {kPassF32, fg_f32_grid(n, p, num_sms)};
   } else {
@@ -567,6 +568,13 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   cudaMemcpyAsync(G_A, d_GA, sizeof(double) * n * r, cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "stmf_fg_host");
+  return STMF_OK;
+}
+
+stmf_status stmf_set_pass_tiles(stmf_ctx_t c, int32_t min_tiles) {
+  if (!c) return STMF_EINVAL;
+  if (min_tiles < 1 || min_tiles > (1 << 20)) return fail(c, STMF_EINVAL, "min_tiles must be in [1, 2^20]");
+  c->min_tiles = min_tiles;
   return STMF_OK;
 }
 

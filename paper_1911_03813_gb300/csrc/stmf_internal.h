@@ -112,10 +112,10 @@ cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s);
 // Tensor-core pass that streams tiles as sub-stages (fg_tc_sub.cu): FP32 samples (each split
 // into two BF16 terms; n <= 256) and BF16 / E4M3 samples with n <= 512; r <= 16.
 bool fg_tc_sub_supported(int dtype, int n, int r);
-int fg_tc_sub_grid(int64_t p, int num_sms);
+int fg_tc_sub_grid(int64_t p, int num_sms, int min_tiles = 1);
 cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
-int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms);
+int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms, int min_tiles = 1);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s);
 int gram_simt_grid(int dtype, int n, int64_t p, int num_sms);
@@ -143,8 +143,10 @@ struct PassPlan {
   PassKind kind;
   int grid;
 };
-// false when no pass holds n x r (the CUDA-core pass's shared memory)
-bool plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather, PassPlan* out);
+// false when no pass holds n x r (the CUDA-core pass's shared memory). min_tiles: the fewest
+// 128-sample tiles a CTA of a tensor-core pass takes (1: one CTA per SM whenever p allows).
+bool plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather, PassPlan* out,
+               int min_tiles = 1);
 cudaError_t launch_pass(const PassPlan& pl, int dtype, const FgParams& prm, cudaStream_t s);
 
 inline int elem_bytes(int dtype) {
@@ -172,6 +174,7 @@ struct stmf_ctx {
   int32_t* status = nullptr; // device status word
   std::string last_error;
   bool profiling = false;    // record events around each fused pass
+  int min_tiles = 1;         // fewest tiles per CTA of a tensor-core pass (serving slots: more)
   std::vector<cudaEvent_t> ev_pool;  // recorded pairs: [2k] start, [2k+1] end
   size_t ev_used = 0;
   // host-streaming evaluation (stmf_fg_host): staging buffers, copy streams, events

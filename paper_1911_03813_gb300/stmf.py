@@ -15,6 +15,7 @@ import torch
 from . import _build
 
 STMF_F64, STMF_F32, STMF_BF16, STMF_E4M3 = 0, 1, 2, 3
+SERVER_PASS_TILES = 128  # STMF_SERVER_PASS_TILES of include/stmf.h
 _TORCH_DTYPE = {
     torch.float64: STMF_F64,
     torch.float32: STMF_F32,
@@ -68,6 +69,8 @@ def lib():
         L.stmf_norm_x_method.argtypes = [vp, ctypes.POINTER(Samples), dp, i32, i32, dp, vp]
         L.stmf_norm_x_method.restype = ctypes.c_int
         L.stmf_profile_enable.argtypes = [vp, i32]
+        L.stmf_set_pass_tiles.argtypes = [vp, i32]
+        L.stmf_set_pass_tiles.restype = ctypes.c_int
         L.stmf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(i64)]
         for name in ("stmf_create", "stmf_destroy", "stmf_reserve", "stmf_device_status",
@@ -110,6 +113,12 @@ class Context:
         if st != 0:
             msg = lib().stmf_last_error(self.handle)
             raise StmfError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def set_pass_tiles(self, min_tiles):
+        """stmf_set_pass_tiles: each CTA of this context's tensor-core passes takes at least
+        min_tiles tiles of 128 samples (1: one CTA per SM; the server's slots use
+        SERVER_PASS_TILES)."""
+        self.check(lib().stmf_set_pass_tiles(self.handle, int(min_tiles)), "stmf_set_pass_tiles")
 
     def device_status(self, stream=None):
         out = ctypes.c_int32()

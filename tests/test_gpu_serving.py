@@ -79,12 +79,16 @@ def test_alone_equals_mix_and_stmf_fit(stmf):
     assert mix["f"] == alone["f"] and mix["best_start"] == alone["best_start"]
     assert torch.equal(lam_m, lam_a) and torch.equal(A_m, A_a)
     assert st["completed"] == 11
-    # the same start through stmf_fit (its own context) gives the same iterate, bit for bit
+    # the same start through stmf_fit (its own context, with the slots' launch shape) gives the
+    # same iterate, bit for bit
     b = alone["best_start"]
     st_dev = inputs.to_storage(_decode(V0), "bf16", device="cuda")
     lam = torch.tensor(x0[b][:r], device="cuda")
     A = torch.tensor(x0[b][r:], device="cuda").reshape(r, n).T   # column-major n x r view
-    res = stmf.fit(st_dev, None, d, lam, A, **opts)
+    ctx = stmf.Context()
+    ctx.set_pass_tiles(stmf.SERVER_PASS_TILES)
+    res = stmf.fit(st_dev, None, d, lam, A, ctx=ctx, **opts)
+    ctx.close()
     assert res["f"] == alone["f"]
     assert torch.equal(lam, lam_a)
 
