@@ -12,9 +12,12 @@
 //         FP32 and b2 keeps its leading 8 bits), region g (features 32g .. 32g + 31) becoming
 //         row by row [b1 of its 32 features | b2 of them]; z = b1 A + b2 A.
 //   BF16  128 features, two TMA boxes of 64 BF16 features, used as they land.
-//   E4M3  128 features, one TMA box of 128 codes landing in region 1 and widened in place into
-//         both regions (every E4M3 value is a BF16 value); the per-sample scale s folds into the
-//         weight, nu' = nu s^d, so z = q^T a with the codes q.
+//   E4M3  128 features, one TMA box of 128 codes landing in a ring of 16 KB code slots of its
+//         own; the converters read a slot into registers, free it for the next copy at once and
+//         write the BF16 values (every E4M3 value is a BF16 value) into both regions of a
+//         sub-stage, so a copy's slot is held only while the copy is in flight and not through
+//         the tile's MMAs; the per-sample scale s folds into the weight, nu' = nu s^d, so
+//         z = q^T a with the codes q.
 // Per sub-stage h of a tile:
 //   MMA1  Z += V_h A_split(features of h)        M = 128 samples, N = 3 RP (16-padded)
 //         (FP32: the b2 products N = 2 RP into their own accumulator)
@@ -67,6 +70,7 @@ struct SubExtra {
   int nsub;        // sub-stages per tile: ceil(n / features per sub-stage)
   int zbufs;       // Z buffers in TMEM: 2 where they fit beside Y, else 1
   int ring;        // sub-stage slots in shared memory
+  int raw;         // E4M3 code slots (16 KB each; 0 for the other storage types)
   int wbufs;       // W buffers: 2, or 1 where a second one would cost a ring slot
   int flush;       // tiles between folds of Y into compensated FP32 registers
   int tmem_cols;
@@ -229,15 +233,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   unsigned char* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
 
   const int R = ex.ring, nsub = ex.nsub, WB = ex.wbufs;
+  const int RR = MODE == kE4M3 ? ex.raw : 0;  // E4M3 code slots
+  const int NF = MODE == kE4M3 ? RR : R;      // slots the TMA copies land in
   const int n = prm.n, r = prm.r, d = prm.d;
   unsigned char* sV = base;                              // ring of R sub-stages
-  unsigned char* sW = sV + size_t(R) * SUB_BYTES;        // WB buffers x 2 regions
+  unsigned char* sRaw = sV + size_t(R) * SUB_BYTES;      // RR code slots (E4M3)
+  unsigned char* sW = sRaw + size_t(RR) * REG_BYTES;     // WB buffers x 2 regions
   unsigned char* sA = sW + size_t(WB) * 2 * C::W_REG;    // nsub x AR regions
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + size_t(nsub * AR) * C::A_REG);
-  uint64_t* full = bars;            // [R] TMA landed
-  uint64_t* conv = bars + R;        // [R] rewritten as BF16 (FP32, E4M3)
-  uint64_t* empty = bars + 2 * R;   // [R] MMA2 done with the sub-stage
-  uint64_t* zfull = bars + 3 * R;  // [ZBUF]
+  uint64_t* full = bars;            // [NF] TMA landed (in a sub-stage, or an E4M3 code slot)
+  uint64_t* conv = full + NF;       // [R] rewritten as BF16 (FP32, E4M3)
+  uint64_t* empty = conv + R;       // [R] MMA2 done with the sub-stage
+  uint64_t* rawfree = empty + R;    // [RR] the converters have read the code slot
+  uint64_t* zfull = rawfree + RR;   // [ZBUF]
   uint64_t* zempty = zfull + 2;
   uint64_t* wfull = zempty + 2;
   uint64_t* wempty = wfull + 2;
@@ -251,11 +259,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
+    for (int s = 0; s < NF; ++s) tc::mbar_init(&full[s], 1);
     for (int s = 0; s < R; ++s) {
-      tc::mbar_init(&full[s], 1);
       tc::mbar_init(&conv[s], NCONV);
       tc::mbar_init(&empty[s], 1);
     }
+    for (int s = 0; s < RR; ++s) tc::mbar_init(&rawfree[s], NCONV);
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&zfull[b], 1);
       tc::mbar_init(&zempty[b], NEPI / 32);
@@ -312,18 +321,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int it = 0; it < my_tiles && ok; ++it) {
         const int64_t tile = blockIdx.x + int64_t(it) * gridDim.x;
         for (int h = 0; h < nsub; ++h) {
-          const int slot = issued % R;
-          if (!tc::mbar_wait_sleep(&empty[slot], ((issued / R) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+          const int slot = issued % NF;
+          // E4M3: the code slot is free once the converters have read it; otherwise the
+          // sub-stage is free once MMA2 is done with it
+          uint64_t* freed = MODE == kE4M3 ? &rawfree[slot] : &empty[slot];
+          if (!tc::mbar_wait_sleep(freed, ((issued / NF) & 1) ^ 1, abortv, WAIT_LIMIT)) {
             fail();
             ok = false;
             break;
           }
-          unsigned char* dst = sV + size_t(slot) * SUB_BYTES;
           const int32_t y0 = (int32_t)(tile * TM);
-          if constexpr (MODE == kE4M3) {  // 128 codes per row, into region 1
+          if constexpr (MODE == kE4M3) {  // 128 codes per row, into a code slot
             tc::mbar_arrive_expect_tx(&full[slot], REG_BYTES);
-            tc::tma_load_2d(dst + REG_BYTES, &tmap, FS * h, y0, &full[slot]);
+            tc::tma_load_2d(sRaw + size_t(slot) * REG_BYTES, &tmap, FS * h, y0, &full[slot]);
           } else {  // two boxes of FS / 2 features (128-byte rows)
+            unsigned char* dst = sV + size_t(slot) * SUB_BYTES;
             tc::mbar_arrive_expect_tx(&full[slot], SUB_BYTES);
             tc::tma_load_2d(dst, &tmap, FS * h, y0, &full[slot]);
             tc::tma_load_2d(dst + REG_BYTES, &tmap, FS * h + FS / 2, y0, &full[slot]);
@@ -332,8 +344,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       // wait for the last copy issued into each slot (already complete unless we aborted)
-      for (int k = issued > R ? issued - R : 0; k < issued; ++k)
-        tc::mbar_wait_sleep(&full[k % R], (k / R) & 1, &no_abort, WAIT_LIMIT);
+      for (int k = issued > NF ? issued - NF : 0; k < issued; ++k)
+        tc::mbar_wait_sleep(&full[k % NF], (k / NF) & 1, &no_abort, WAIT_LIMIT);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA1 issuer
@@ -444,8 +456,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // row y sits at chunk position c ^ (y & 7) in either layout).
     // FP32: per region, the 32 FP32 values of the row become b1 of the 32 features (BF16 chunks
     //       0-3) and b2 (chunks 4-7).
-    // E4M3: the 128 codes of the row (region 1) become the BF16 values of features 0-63 (region
-    //       0) and 64-127 (region 1); all codes are read before anything is written.
+    // E4M3: the 128 codes of the row (row y of a code slot, the same swizzle) are read into
+    //       registers, the slot is released, and once MMA2 is done with the sub-stage's last use
+    //       they are written as the BF16 values of features 0-63 (region 0) and 64-127
+    //       (region 1).
     if constexpr (CONVERT) {
       const int y = tid - CONV0;
       const uint32_t sw = uint32_t(y & 7);
@@ -454,7 +468,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int h = 0; h < nsub; ++h, ++seq) {
           const int slot = seq % R;
-          if (!tc::mbar_wait_sleep(&full[slot], (seq / R) & 1, abortv, WAIT_LIMIT)) {
+          const int fs = seq % NF;
+          if (!tc::mbar_wait_sleep(&full[fs], (seq / NF) & 1, abortv, WAIT_LIMIT)) {
             ok = false;
             break;
           }
@@ -482,10 +497,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           } else {
             unsigned char* row1 = row0 + REG_BYTES;
+            const unsigned char* src = sRaw + size_t(fs) * REG_BYTES + y * 128;
             uint4 raw[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-              raw[c] = *reinterpret_cast<const uint4*>(row1 + ((uint32_t(c) ^ sw) << 4));
+              raw[c] = *reinterpret_cast<const uint4*>(src + ((uint32_t(c) ^ sw) << 4));
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&rawfree[fs]);
+            if (!tc::mbar_wait_sleep(&empty[slot], ((seq / R) & 1) ^ 1, abortv, WAIT_LIMIT)) {
+              ok = false;
+              break;
+            }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {  // codes 16c .. 16c + 15 -> BF16 chunks 2c, 2c + 1
               unsigned char* dst = (c < 4) ? row0 : row1;
@@ -729,18 +751,33 @@ SubExtra plan_sub(int mode, int n, int r) {
   ex.nsub = (n + fs - 1) / fs;
   const int RP = rp_of(r), N1 = (3 * RP + 15) / 16 * 16, N2 = 2 * RP;
   const int a_bytes = ex.nsub * (fs / 64) * N1 * 128;
-  // W buffers, A split, 1024 bytes of alignment slack and 1024 of barriers and w sums; a
-  // second W buffer lets the epilogue write W(t+1) while MMA2 still reads W(t), but a deeper
-  // ring matters more: keep six sub-stage slots when the A split of many features needs the room
-  int fixed = 0, R = 0;
-  for (ex.wbufs = 2; ex.wbufs >= 1; --ex.wbufs) {
-    fixed = ex.wbufs * 2 * N2 * 128 + a_bytes + 1024 + 1024;
-    R = (int(kMaxSmem) - fixed) / SUB_BYTES;
-    if (R >= 6) break;
+  // W buffers, E4M3 code slots, A split, 1024 bytes of alignment slack and 1024 of barriers and w
+  // sums. A second W buffer lets the epilogue write W(t+1) while MMA2 still reads W(t); the ring
+  // wants six sub-stages (FP32, BF16: each is held from its copy to its MMA2 block) or two tiles'
+  // worth (E4M3: copies land in the code slots, so a sub-stage is held only from its widening
+  // on); E4M3 takes as many code slots (copies in flight) as fit beside that.
+  static const int kRawE4M3[3] = {4, 3, 2}, kRawNone[1] = {0};
+  const int* raw_opts = mode == kE4M3 ? kRawE4M3 : kRawNone;
+  const int n_raw = mode == kE4M3 ? 3 : 1;
+  const int want = mode == kE4M3 ? 2 * ex.nsub : 6;
+  int best = -1;
+  for (int k = 0; k < n_raw; ++k) {
+    const int rr = raw_opts[k];
+    for (int wb = 2; wb >= 1; --wb) {
+      const int fixed = wb * 2 * N2 * 128 + a_bytes + rr * REG_BYTES + 1024 + 1024;
+      int R = (int(kMaxSmem) - fixed) / SUB_BYTES;
+      if (R > 8) R = 8;
+      if (R < 1) continue;
+      const int score = (R < want ? R : want) * 100 + rr * 10 + wb;
+      if (score > best) {
+        best = score;
+        ex.ring = R;
+        ex.raw = rr;
+        ex.wbufs = wb;
+        ex.smem_bytes = fixed + R * SUB_BYTES;
+      }
+    }
   }
-  if (ex.wbufs < 1) ex.wbufs = 1;
-  if (R > 8) R = 8;
-  ex.ring = R;
   ex.flush = 8;
   const int zbs = 2 * ((N1 + 2 * RP - 1) / (2 * RP) * (2 * RP)) + 2 * RP;
   ex.zbufs = tmem_need(zbs, 2, ex.nsub, N2) <= 512 ? 2 : 1;
@@ -748,7 +785,6 @@ SubExtra plan_sub(int mode, int n, int r) {
   int pow2 = 32;
   while (pow2 < cols) pow2 <<= 1;
   ex.tmem_cols = pow2;
-  ex.smem_bytes = fixed + R * SUB_BYTES;
   return ex;
 }
 
