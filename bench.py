@@ -373,11 +373,13 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
 
 
 def gram_bench(dev):
-    """One ||X||^2 Gram pass (tensor cores, BF16) on the first 2^16 samples of the workload."""
+    """One ||X||^2 Gram pass (tensor cores, BF16) on the first 2^18 samples of the workload (the
+    pass is O(p^2 n): 1.8e13 FLOP here; with 2^16 samples, about 14 work items per CTA, the tail
+    and the I-tile reloads show)."""
     import torch
 
     from paper_1911_03813_gb300 import inputs, stmf
-    p = 1 << 16
+    p = 1 << 18
     st = inputs.gmm_device(N_FEAT, p, N_MEANS, SIGMA, SEED, dev, out_dtype="bf16")
     stmf.norm_x(st, None, D)
     torch.cuda.synchronize()
@@ -586,7 +588,7 @@ def main():
     ap.add_argument("--alpha-only", action="store_true",
                     help="only ||X||^2 from the distinct entries of X at n=100, p=2.5e6, d=3")
     ap.add_argument("--gram-only", action="store_true",
-                    help="time only the ||X||^2 Gram pass on 2^16 samples and print it")
+                    help="time only the ||X||^2 Gram pass on 2^18 samples and print it")
     ap.add_argument("--legs", default="bf16,fp32,fp8",
                     help="sample types to time (bf16 is the headline)")
     ap.add_argument("--oracle-one-core", nargs=2, type=float, default=None,

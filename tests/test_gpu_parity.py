@@ -261,9 +261,13 @@ def test_fg_full_size(stmf, dtype, n, p, r, d, sigma):
 
 @pytest.mark.parametrize("n,p,d,weights", [(256, 1 << 15, 4, None), (100, 20000, 3, None),
                                            (64, 9000, 2, "nonuniform"), (33, 3001, 4, "nonuniform"),
-                                           (256, 1200, 3, None), (17, 129, 4, None)])
+                                           (256, 1200, 3, None), (17, 129, 4, None),
+                                           (48, 128, 3, None), (130, 4100, 4, "nonuniform"),
+                                           (200, 40000, 2, "nonuniform")])
 def test_norm_x_tensor_core_parity(stmf, n, p, d, weights):
-    """BF16 samples take the tensor-core Gram pass: several J chunks, ragged tiles, nu given."""
+    """BF16 samples take the tensor-core Gram pass: several J chunks, ragged tiles, nu given; an
+    odd number of tiles (the last I tile has no partner), one tile alone, 33 tiles (one past a
+    chunk of 32) and 313 tiles (10 chunks)."""
     data = inputs.gmm(n, p, 8, 0.1, seed=n + p)
     st = inputs.to_storage(data["V"], "bf16", device="cuda")
     nu = inputs.positive_weights(p, seed=p) if weights else None
