@@ -502,7 +502,6 @@ stmf_status stmf_fg_host(stmf_ctx_t c, const stmf_samples* V, const double* nu, 
   const size_t small = sizeof(double) * (r + n * r + 1 + L + 1 + r + n * r);
   if (small > c->host_small_bytes) {
     if (c->host_small) cudaFree(c->host_small);
-  if (c->sym_dev) cudaFree(c->sym_dev);
     c->host_small = nullptr;
     c->host_small_bytes = 0;
     if (cudaMalloc(&c->host_small, small) != cudaSuccess)

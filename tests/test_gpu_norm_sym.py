@@ -92,3 +92,24 @@ def test_compressed_limits(stmf):
     st = inputs.to_storage(data["V"], "f32", device="cuda")
     with pytest.raises(stmf.StmfError):
         stmf.norm_x(st, None, 5, method="compressed")
+
+
+def test_prefix_table_survives_host_calls(stmf):
+    """A context's host-buffer evaluations (stmf_fg_host) grow their small device buffers without
+    touching the compressed-norm prefix table: alpha before and after host calls of growing r
+    agrees bit for bit, and the context is destroyed cleanly afterwards."""
+    ctx = stmf.Context()
+    n, p, d = 40, 5000, 3
+    data = inputs.gmm(n, p, 4, 0.1, seed=11)
+    st = inputs.to_storage(data["V"], "f32", device="cuda")
+    a0 = stmf.norm_x(st, None, d, method="compressed", ctx=ctx).item()
+    host = inputs.to_storage(data["V"], "f32", device="cpu")
+    for r in (2, 8, 16):
+        lam, A = inputs.random_model(n, r, seed=r)
+        f, _, _ = stmf.fg_host(host, None, d, lam, A, alpha=a0, ctx=ctx)
+        assert np.isfinite(f)
+    a1 = stmf.norm_x(st, None, d, method="compressed", ctx=ctx).item()
+    torch.cuda.synchronize()
+    assert a1 == a0
+    assert ctx.device_status() == 0
+    ctx.close()
