@@ -309,10 +309,12 @@ def make_requests(count, seed, dev, pool=256):
     return out
 
 
-def serving_bench(n_requests, seed, dev, device_index, sweep=()):
+def serving_bench(n_requests, seed, dev, device_index, sweep=(), fixed_rate=80.0):
     """Continuous batching through stmf_server_*: a saturated run fixes the capacity, then Poisson
     arrivals at 0.8x that rate give the latency percentiles; `sweep` lists further multiples of
-    the saturated rate, each run on the same requests with its own arrival draw."""
+    the saturated rate, each run on the same requests with its own arrival draw. A last run
+    offers a quarter of the requests at a fixed rate (`fixed_rate` requests/s, 4 fits each), so
+    the latency can be compared at the same load across versions whose capacity differs."""
     import numpy as np
 
     from paper_1911_03813_gb300 import stmf
@@ -320,12 +322,13 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
     sat = make_requests(max(n_requests // 4, 8), seed, dev)
     poi = make_requests(n_requests, seed + 1, dev)
 
-    def poisson(srv, rate, draw_seed):
-        gaps = np.random.default_rng(draw_seed).exponential(1.0 / rate, size=len(poi))
+    def poisson(srv, rate, draw_seed, reqs=None):
+        reqs = poi if reqs is None else reqs
+        gaps = np.random.default_rng(draw_seed).exponential(1.0 / rate, size=len(reqs))
         t0 = time.perf_counter()
         due = t0
         tick = []
-        for q, gap in zip(poi, gaps):
+        for q, gap in zip(reqs, gaps):
             due += gap
             while time.perf_counter() < due:
                 time.sleep(0.0002)
@@ -333,7 +336,7 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
         res = [srv.poll(t) for t in tick]
         el = time.perf_counter() - t0
         lat = np.array([r_["t_done"] - r_["t_submit"] for r_ in res]) * 1e3
-        return {"arrival_rate_per_s": rate, "fits_per_s": 4 * len(poi) / el,
+        return {"arrival_rate_per_s": rate, "fits_per_s": 4 * len(reqs) / el,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "completed": int(sum(r_["state"] == 0 for r_ in res))}
 
@@ -354,6 +357,10 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
             row = poisson(srv, mult * rate_sat, seed + 3 + k)
             row["rate_over_saturated"] = mult
             extra.append(row)
+        fixed = None
+        if fixed_rate and fixed_rate < rate_sat:
+            fixed = poisson(srv, fixed_rate, seed + 99, poi[:max(len(poi) // 4, 8)])
+            fixed["requests"] = max(len(poi) // 4, 8)
         stats = srv.stats()
     out = {"requests": len(poi), "starts_per_request": 4,
            "workload": "n, p log-uniform in [8,128] x [1e3,1e6], d in {3,4}, r in [1,16], "
@@ -369,6 +376,8 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=()):
            "optimiser": "L-BFGS m=5, pgtol 1e-5, factr 1e9, <= 200 evaluations per start"}
     if extra:
         out["sweep"] = extra
+    if fixed is not None:
+        out["at_fixed_rate"] = fixed
     return out
 
 
