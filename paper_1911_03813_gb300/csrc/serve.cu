@@ -298,34 +298,43 @@ extern "C" stmf_status stmf_server_create(const stmf_server_config* cfg, stmf_se
   srv->cfg = *cfg;
   srv->t0 = Clock::now();
   if (cudaSetDevice(cfg->device) != cudaSuccess) return STMF_EINVAL;
+  // a failure part-way releases whatever was built (destroy skips what was not: no thread yet,
+  // null handles)
+  auto bail = [&srv](stmf_status st) {
+    stmf_server_destroy(srv.release());
+    return st;
+  };
   // the largest workspaces any request may need (every storage type at n_max, r_max)
   const long long Dmax = cfg->r_max + (long long)cfg->n_max * cfg->r_max;
   srv->slots.resize(cfg->max_fits);
   for (auto& s : srv->slots) {
     stmf_status st = stmf_create(cfg->device, &s.ctx);
-    if (st != STMF_OK) return st;
+    if (st != STMF_OK) return bail(st);
     // many small fits run at once: a tensor-core pass takes whole SMs, so each CTA of a slot's
     // pass takes at least kSlotTiles tiles and the passes of other slots find SMs free
     stmf_set_pass_tiles(s.ctx, kSlotTiles);
     const size_t ws = stmf::fg_workspace_bytes_any(s.ctx, cfg->n_max, cfg->r_max);
     st = stmf::ensure_workspace(s.ctx, ws);
-    if (st != STMF_OK) return st;
+    if (st != STMF_OK) return bail(st);
     const size_t fb = stmf::fit_state_bytes(Dmax, cfg->m_max);
-    if (cudaMalloc(&s.ctx->fit_ws, fb) != cudaSuccess) return STMF_ENOMEM;
+    if (cudaMalloc(&s.ctx->fit_ws, fb) != cudaSuccess) {
+      s.ctx->fit_ws = nullptr;
+      return bail(STMF_ENOMEM);
+    }
     s.ctx->fit_ws_bytes = fb;
     srv->slot_bytes += s.ctx->ws_bytes + fb;
     if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s.host_words, 2 * sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost(&s.state_host, stmf::FitRun::state_size()) != cudaSuccess)
-      return STMF_ECUDA;
+      return bail(STMF_ECUDA);
   }
-  if (srv->slot_bytes > cfg->mem_budget) return STMF_ENOMEM;
+  if (srv->slot_bytes > cfg->mem_budget) return bail(STMF_ENOMEM);
   srv->avail = cfg->mem_budget - srv->slot_bytes;
   srv->stats.slot_bytes = srv->slot_bytes;
   if (cudaStreamCreateWithFlags(&srv->admin, cudaStreamNonBlocking) != cudaSuccess)
-    return STMF_ECUDA;
-  if (cudaDeviceSynchronize() != cudaSuccess) return STMF_ECUDA;
+    return bail(STMF_ECUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(STMF_ECUDA);
   stmf_server* raw = srv.get();
   srv->thr = std::thread([raw]() { raw->run(); });
   *out = srv.release();

@@ -612,6 +612,7 @@ stmf_status norm_x_sym(stmf_ctx* c, const stmf_samples* V, const double* nu, int
   if (stmf::norm_sym_smem(V->dtype, n) > kMaxSmem - 1024)
     return fail(c, STMF_EINVAL, "n too large for the compressed tensor (shared memory)");
   if (c->sym_n != n || c->sym_d != d || !c->sym_dev) {
+    c->sym_n = c->sym_d = -1;  // no valid table until the upload below succeeds
     std::vector<stmf::SymPrefix> tab;
     stmf::sym_prefixes(n, d, tab);
     const size_t bytes = tab.size() * sizeof(stmf::SymPrefix);
