@@ -381,6 +381,46 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=(), fixed_rate=80.0
     return out
 
 
+def other_passes_bench(st16, st32, lam_t, A_t, dev):
+    """The other passes over the samples, on the headline workload's samples (2^24 x 256): the
+    range finder of eq. rrf (A0 = V Omega with r_hat = 16, Omega drawn inside the pass; one read
+    of the BF16 V, CUDA cores) and the sampled evaluation of Sec. 5 (Lemma 5.1) on 2^20 rows
+    gathered at random from the BF16 and the FP32 copy (CUDA-core gather passes), each against
+    the HBM copy peak over the bytes it reads."""
+    import torch
+
+    from paper_1911_03813_gb300 import stmf
+    peaks = measured_peaks()
+    p, n = st16["data"].shape[0], st16["n"]
+
+    def events(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_rrf = events(lambda: stmf.rrf_start(st16, 16, 7), 5)
+    gb_rrf = p * n * 2 / (ms_rrf / 1e3) / 1e9
+    s = 1 << 20
+    idx = torch.randint(0, p, (s,), device=dev, dtype=torch.int64,
+                        generator=torch.Generator(device=dev).manual_seed(SEED))
+    out = {"rrf_start": {"n": n, "p": p, "r_hat": 16, "dtype": "bf16", "ms": ms_rrf,
+                         "gbs_over_V": gb_rrf, "frac_of_hbm": gb_rrf / peaks["hbm_gbs"]}}
+    for name, st, eb in (("sampled_fg_bf16", st16, 2), ("sampled_fg_f32", st32, 4)):
+        if st is None:
+            continue
+        ms_smp = events(lambda: stmf.fg_sampled(st, idx, D, lam_t, A_t), 20)
+        gb_smp = s * n * eb / (ms_smp / 1e3) / 1e9
+        out[name] = {"n": n, "rows": s, "r": R, "d": D, "ms": ms_smp, "gbs_over_rows": gb_smp,
+                     "frac_of_hbm": gb_smp / peaks["hbm_gbs"], "row_draw": "uniform, with replacement"}
+    return out
+
+
 def gram_bench(dev):
     """One ||X||^2 Gram pass (tensor cores, BF16) on the first 2^18 samples of the workload (the
     pass is O(p^2 n): 1.8e13 FLOP here; with 2^16 samples, about 14 work items per CTA, the tail
@@ -770,6 +810,7 @@ def main():
 
     if rank != 0:
         return
+    other = None if args.no_gram else other_passes_bench(st16, st32, lam_t, A_t, dev)
     del st16, st32, st8
     torch.cuda.empty_cache()
     gram = None if args.no_gram else gram_bench(dev)
@@ -811,6 +852,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "e2e": e2e,
         "gram": gram,
+        "other_passes": other,
         "alpha_fp32_scale": alpha,
         "fp32_scale": fp32_scale,
         "differentiation": differentiation,

@@ -377,8 +377,10 @@ STMF_API stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats*
  * unit-norm columns, Omega a p x r_hat Gaussian test matrix. Omega is never stored: entry (l, j)
  * is drawn inside the pass from Philox4x32-10 (Salmon et al., SC 2011) with counter
  * (l mod 2^32, l div 2^32, j, 0) and key (seed mod 2^32, seed div 2^32); the first two output
- * words give u1, u2 = (x + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). The
- * sums are FP64.
+ * words give u1, u2 = (x + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). FP64
+ * samples: the draw, products and sums in FP64. Other samples: the draw and products in FP32 and
+ * sums in FP32 over 16 tiles, folded into FP64 (about 1e-6 relative to the FP64 result); the
+ * column normalisation is FP64.
  *  V        samples (any type).     r_hat  1..64 columns (n * r_hat limited by shared memory).
  *  seed     key of the generator.   A0     device, n x r_hat FP64 column-major (out).
  * Enqueued on `stream`; asynchronous.

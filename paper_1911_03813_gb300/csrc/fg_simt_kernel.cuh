@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "rrf_draw.cuh"
 #include "stmf_internal.h"
 
 namespace stmf {
@@ -67,31 +68,6 @@ size_t smem_bytes(int n, int rp, int TS) {
   b += up16(sizeof(TC) * TS);                            // nus[TS]
   b += up16(sizeof(double) * (NT / 32) * 16);            // wsh[warps][16]
   return b;
-}
-
-// Philox4x32-10 (Salmon et al., SC 2011) and a Box-Muller normal: entry (l, j) of the test matrix
-// of eq. rrf uses counter (l mod 2^32, l div 2^32, j, 0) and key (seed mod 2^32, seed div 2^32);
-// words x0, x1 give u_k = (x_k + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2).
-__device__ __forceinline__ double rrf_omega(int64_t l, int j, uint64_t seed) {
-  uint32_t c0 = (uint32_t)(uint64_t)l, c1 = (uint32_t)((uint64_t)l >> 32), c2 = (uint32_t)j, c3 = 0;
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-#pragma unroll
-  for (int rnd = 0; rnd < 10; ++rnd) {
-    if (rnd > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-  }
-  const double u1 = ((double)c0 + 0.5) * 0x1p-32;
-  const double u2 = ((double)c1 + 0.5) * 0x1p-32;
-  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
 // RRF = false: the fused pass of Alg. 2. RRF = true: the randomized range finder of eq. rrf,
@@ -187,7 +163,12 @@ __global__ void __launch_bounds__(NT) fg_simt_kernel(const FgParams prm) {
       // phase 1 (range finder): W = the rows of the Gaussian test matrix for these samples
       for (int e = tid; e < TS * rp; e += NT) {
         const int s = e / rp, j = e - (e / rp) * rp;
-        Ws[e] = (s < valid && j < r) ? (TC)rrf_omega(s0 + s, j, prm.seed) : (TC)0;
+        TC om = (TC)0;
+        if (s < valid && j < r) {
+          if constexpr (sizeof(TC) == 4) om = rrf_omega_f32(s0 + s, j, prm.seed);
+          else om = (TC)rrf_omega(s0 + s, j, prm.seed);
+        }
+        Ws[e] = om;
       }
     } else
     // phase 1: z = v_s^T a_j for the thread's sample s and column quads q0, q0 + QG, ...

@@ -4,9 +4,9 @@
 
 namespace stmf {
 
-int rrf_grid(int, int n, int r, int64_t p, int num_sms) {
-  // the FP64 grid (one block per SM) serves both variants of the range finder
-  return fg_simt_grid(STMF_F64, n, r, p, num_sms);
+int rrf_grid(int, int n, int r, int64_t p, int num_sms, bool f64) {
+  // each variant takes the grid of its accumulator type (FP64: one block per SM; FP32: up to two)
+  return fg_simt_grid(f64 ? STMF_F64 : STMF_F32, n, r, p, num_sms);
 }
 
 cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s, bool f64) {

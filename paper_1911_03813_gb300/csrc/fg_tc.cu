@@ -31,6 +31,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include "rrf_draw.cuh"
 #include "stmf_internal.h"
 #include "tc_common.cuh"
 
@@ -117,7 +118,11 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 //              BF16 value) before the MMAs read the stage; the scale folds into the weight,
 //              nu' = nu s^d: with z = q^T a, the terms of eq. Y and Lemma 3.5 are nu' z^{d-1} q
 //              and nu' z^d.
-template <int RP, bool FP8>
+// RRF = true:  the randomized range finder of eq. rrf, Y_part = sum_l v_l omega_l^T: no MMA1 and
+//              no w; the epilogue draws row l of the Gaussian test matrix (Philox4x32-10, FP32
+//              Box-Muller; times s_l for E4M3) as W, and MMA2 accumulates V^T W as above. MMA2
+//              then waits for the staged tile itself, which MMA1 otherwise orders.
+template <int RP, bool FP8, bool RRF>
 __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
   constexpr int NT = FP8 ? NTHREADS_FP8 : NTHREADS;
@@ -176,10 +181,10 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
 
   // A split: the hi row of component j holds BF16(a_j), its lo row BF16(a_j - BF16(a_j)); K =
-  // feature.
+  // feature (not used by the range finder).
   {
     const int kext = nreg * 64;
-    for (int e = tid; e < N * kext; e += NT) {
+    for (int e = tid; e < (RRF ? 0 : N * kext); e += NT) {
       const int row = e / kext, k = e - row * kext;
       const int grp = row / (2 * C::CPG), part = (row / C::CPG) & 1;
       const int j = grp * C::CPG + row % C::CPG;
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA1 issuer
     // Z(t) = V_t [A_hi | A_lo] as soon as tile t has landed and its Z buffer is free.
-    if (lane == 0) {
+    if (!RRF && lane == 0) {
       const uint32_t idesc1 = tc::idesc_bf16(128, N, 0, 0);  // V K-major, A split K-major
       const int k1 = (n + 15) / 16;
       // shared-memory descriptors are linear in the operand address (16-byte units in the low
@@ -299,6 +304,8 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
         const bool first = (t % flush) == 0;
         if (first) ok = tc::mbar_wait(&yempty[yb], ((period >> 1) & 1) ^ 1, abortv, WAIT_LIMIT);
         ok = ok && tc::mbar_wait(&wfull[wb], (t >> 1) & 1, abortv, WAIT_LIMIT);
+        if constexpr (RRF)  // no MMA1 has waited for this tile
+          ok = ok && tc::mbar_wait(FP8 ? &conv[st] : &full[st], (t / S) & 1, abortv, WAIT_LIMIT);
         if (!ok) break;
         tc::tc_fence_after();
         const uint64_t wd = wdesc0 + uint64_t((uint32_t(wb) * 2 * C::W_REG) >> 4);
@@ -440,37 +447,47 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     for (int it = 0; it < my_tiles; ++it) {
       const int zb = it & 1, wb = it & 1;
       float nu_s = nu_next;
-      if constexpr (FP8) {  // nu' = nu s^d (the scale of sample l folded into its weight), FP32
-        const float sc = sc_next;
-        float sd = sc;
-        for (int e = 1; e < d; ++e) sd *= sc;
+      const float sc_cur = sc_next;
+      if constexpr (FP8 && !RRF) {  // nu' = nu s^d (the scale of sample l folded into its weight)
+        float sd = sc_cur;
+        for (int e = 1; e < d; ++e) sd *= sc_cur;
         nu_s *= sd;
       }
       load_weight(it + 1);
-      if (!tc::mbar_wait(&zfull[zb], (it >> 1) & 1, abortv, WAIT_LIMIT)) {
-        ok = false;
-        break;
-      }
-      tc::tc_fence_after();
-      // z = sum over the Z accumulators of (hi + lo), rounded to nearest in FP32: each
-      // accumulator takes only kpz truncating tensor-core accumulations
-      float zv[ZC][2 * CPG];  // per accumulator: hi of the group's components, then lo
-#pragma unroll
-      for (int c = 0; c < ZC; ++c)
-        tmem_load_cols<2 * CPG>(tmem + uint32_t(zb * ZC + c) * N + 2 * j0 + lane_off, zv[c]);
-      tc::tmem_ld_wait();
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&zempty[zb]);
       float wv[CPG];
+      if constexpr (RRF) {
+        // W row of sample l: omega_lj (s_l omega_lj for E4M3 codes), zero past p and past r
+        const int64_t sidx = (blockIdx.x + int64_t(it) * gridDim.x) * TM + L;
 #pragma unroll
-      for (int c = 0; c < CPG; ++c) {
-        float zz = zv[0][c] + zv[0][CPG + c];
+        for (int c = 0; c < CPG; ++c)
+          wv[c] = (sidx < prm.p && j0 + c < r)
+                      ? (FP8 ? sc_cur : 1.f) * rrf_omega_f32(sidx, j0 + c, prm.seed)
+                      : 0.f;
+      } else {
+        if (!tc::mbar_wait(&zfull[zb], (it >> 1) & 1, abortv, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        // z = sum over the Z accumulators of (hi + lo), rounded to nearest in FP32: each
+        // accumulator takes only kpz truncating tensor-core accumulations
+        float zv[ZC][2 * CPG];  // per accumulator: hi of the group's components, then lo
 #pragma unroll
-        for (int k = 1; k < ZC; ++k) zz += zv[k][c] + zv[k][CPG + c];
-        const float t = ipow_f(zz, d - 1);
-        wv[c] = nu_s * t;
-        wacc[c] += wv[c] * zz;
+        for (int c = 0; c < ZC; ++c)
+          tmem_load_cols<2 * CPG>(tmem + uint32_t(zb * ZC + c) * N + 2 * j0 + lane_off, zv[c]);
+        tc::tmem_ld_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&zempty[zb]);
+#pragma unroll
+        for (int c = 0; c < CPG; ++c) {
+          float zz = zv[0][c] + zv[0][CPG + c];
+#pragma unroll
+          for (int k = 1; k < ZC; ++k) zz += zv[k][c] + zv[k][CPG + c];
+          const float t = ipow_f(zz, d - 1);
+          wv[c] = nu_s * t;
+          wacc[c] += wv[c] * zz;
+        }
       }
       if (!tc::mbar_wait(&wempty[wb], ((it >> 1) & 1) ^ 1, abortv, WAIT_LIMIT)) {
         ok = false;
@@ -536,10 +553,12 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
             if (j0 + c < r) {
               const double y = (double)ys[mb][c] - (double)yc[mb][c];
               part[r + i + size_t(n) * (j0 + c)] = y;
-              const double a = prm.A[i + size_t(n) * (j0 + c)];
-              const double hi = (double)__bfloat162float(__double2bfloat16(a));
-              const double lo = (double)__bfloat162float(__double2bfloat16(a - hi));
-              corr[c] += y * ((a - hi) - lo);
+              if constexpr (!RRF) {
+                const double a = prm.A[i + size_t(n) * (j0 + c)];
+                const double hi = (double)__bfloat162float(__double2bfloat16(a));
+                const double lo = (double)__bfloat162float(__double2bfloat16(a - hi));
+                corr[c] += y * ((a - hi) - lo);
+              }
             }
         }
       }
@@ -608,13 +627,14 @@ TcExtra plan(int n, int r, bool) {  // the same staging serves BF16 and E4M3 sam
   return ex;
 }
 
-template <int RP, bool FP8>
+template <int RP, bool FP8, bool RRF>
 cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtra& ex, int grid,
                       cudaStream_t s) {
-  const cudaError_t e = smem_limit((const void*)fg_tc_kernel<RP, FP8>, 232448);
+  const cudaError_t e = smem_limit((const void*)fg_tc_kernel<RP, FP8, RRF>, 232448);
   if (e != cudaSuccess) return e;
-  return launch_kernel(fg_tc_kernel<RP, FP8>, dim3(grid), dim3(FP8 ? NTHREADS_FP8 : NTHREADS),
-                       size_t(ex.smem_bytes), s, tmap, prm, ex);
+  return launch_kernel(fg_tc_kernel<RP, FP8, RRF>, dim3(grid),
+                       dim3(FP8 ? NTHREADS_FP8 : NTHREADS), size_t(ex.smem_bytes), s, tmap, prm,
+                       ex);
 }
 
 }  // namespace
@@ -637,7 +657,10 @@ int fg_tc_grid(int, int, int, int64_t p, int num_sms, int min_tiles) {
   return (int)(want < num_sms ? want : num_sms);
 }
 
-cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+namespace {
+
+template <bool RRF>
+cudaError_t launch_tc(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
   if (dtype != STMF_BF16 && dtype != STMF_E4M3) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
   EncodeFn enc = get_encode();
@@ -655,11 +678,21 @@ cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t 
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const TcExtra ex = plan(prm.n, prm.r, fp8);
   if (fp8) {
-    if (rp_of(prm.r) == 8) return launch_rp<8, true>(tmap, prm, ex, grid, s);
-    return launch_rp<16, true>(tmap, prm, ex, grid, s);
+    if (rp_of(prm.r) == 8) return launch_rp<8, true, RRF>(tmap, prm, ex, grid, s);
+    return launch_rp<16, true, RRF>(tmap, prm, ex, grid, s);
   }
-  if (rp_of(prm.r) == 8) return launch_rp<8, false>(tmap, prm, ex, grid, s);
-  return launch_rp<16, false>(tmap, prm, ex, grid, s);
+  if (rp_of(prm.r) == 8) return launch_rp<8, false, RRF>(tmap, prm, ex, grid, s);
+  return launch_rp<16, false, RRF>(tmap, prm, ex, grid, s);
+}
+
+}  // namespace
+
+cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_tc<false>(dtype, prm, grid, s);
+}
+
+cudaError_t fg_tc_rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_tc<true>(dtype, prm, grid, s);
 }
 
 }  // namespace stmf

@@ -369,12 +369,18 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   if (r_hat < 1 || r_hat > 64) return fail(c, STMF_EINVAL, "r_hat must be in [1, 64]");
   if (!A0) return fail(c, STMF_EINVAL, "A0 is NULL");
   const int n = (int)V->n;
-  // FP64 products and sums while a 64-sample FP64 tile fits in shared memory; beyond that (large
-  // n) FP32 products with FP32 sums over 16 tiles folded into FP64
-  const bool f64 = stmf::fg_simt_smem(STMF_F64, n, (int)r_hat) <= kMaxSmem;
-  if (!f64 && stmf::fg_simt_smem(STMF_F32, n, (int)r_hat) > kMaxSmem)
+  // BF16 and E4M3 samples with n <= 256 and r_hat <= 16: the tensor-core pass (the test matrix
+  // drawn in FP32 as its W, hi/lo BF16 products, FP32 accumulation folded every 8 tiles).
+  // FP64 samples: FP64 draws, products and sums on the CUDA cores (an FP64 tile must fit in
+  // shared memory). Other samples: FP32 draws and products on the CUDA cores, FP32 sums over 16
+  // tiles folded into FP64 (FP64 arithmetic runs at a small fraction of the FP32 rate on this
+  // part, and A0 is a random start).
+  const bool tcore = stmf::fg_tc_supported(V->dtype, n, (int)r_hat) != 0;
+  const bool f64 = V->dtype == STMF_F64;
+  if (!tcore && stmf::fg_simt_smem(f64 ? STMF_F64 : STMF_F32, n, (int)r_hat) > kMaxSmem)
     return fail(c, STMF_EINVAL, "n * r_hat too large for the range finder (shared memory)");
-  const int grid = stmf::rrf_grid(V->dtype, n, (int)r_hat, V->p, c->num_sms);
+  const int grid = tcore ? stmf::fg_tc_grid(V->dtype, n, (int)r_hat, V->p, c->num_sms, c->min_tiles)
+                         : stmf::rrf_grid(V->dtype, n, (int)r_hat, V->p, c->num_sms, f64);
   const size_t L = size_t(r_hat) + size_t(n) * size_t(r_hat);
   st = ensure_ws(c, (size_t(grid) * L + L) * sizeof(double));
   if (st != STMF_OK) return st;
@@ -384,6 +390,7 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   stmf::FgParams prm{};
   prm.V = V->data;
   prm.scale = V->scale;
+  prm.nu_uniform = 1.0;
   prm.partials = partials;
   prm.p = V->p;
   prm.n = n;
@@ -394,7 +401,8 @@ stmf_status stmf_rrf_start(stmf_ctx_t c, const stmf_samples* V, int64_t r_hat, u
   prm.flush_tiles = f64 ? 1 << 30 : 16;  // FP64 accumulators need no intermediate folds
   prm.status = c->status;
   prm.seed = seed;
-  cudaError_t e = stmf::rrf_launch(V->dtype, prm, grid, s, f64);
+  cudaError_t e = tcore ? stmf::fg_tc_rrf_launch(V->dtype, prm, grid, s)
+                        : stmf::rrf_launch(V->dtype, prm, grid, s, f64);
   if (e != cudaSuccess) return cuda_fail(c, e, "range finder launch");
   stmf::ModelParams mp{};
   mp.partials = partials;

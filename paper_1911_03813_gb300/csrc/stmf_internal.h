@@ -99,7 +99,7 @@ cudaError_t fg_simt_launch_f64(const FgParams& prm, int grid, cudaStream_t s);
 // Randomized range finder (eq. rrf): block partials of V Omega into prm.partials (w part zero).
 // f64: FP64 products and sums (needs fg_simt_smem(STMF_F64, n, r) <= 232448), else FP32 products
 // with FP32 sums folded into FP64 every prm.flush_tiles tiles.
-int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms);
+int rrf_grid(int dtype, int n, int r, int64_t p, int num_sms, bool f64);
 cudaError_t rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s, bool f64);
 // Sum the block partials only (no model terms): yw = sum_g partials[g].
 cudaError_t reduce_partials_launch(const ModelParams& prm, cudaStream_t s);
@@ -117,6 +117,8 @@ cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStrea
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms, int min_tiles = 1);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+// the range finder of eq. rrf on the same pass (Y partials of V Omega, w = 0; prm.seed)
+cudaError_t fg_tc_rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s);
 int gram_simt_grid(int dtype, int n, int64_t p, int num_sms);
 bool gram_tc_supported(int dtype, int n, int64_t p);
