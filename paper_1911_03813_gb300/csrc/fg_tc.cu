@@ -99,6 +99,19 @@ __device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint16_t q) {
   return *reinterpret_cast<const uint32_t*>(&bb);
 }
 
+// 16-byte global -> shared copy of which the first `bytes` are read (the rest zero-filled).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int C>
 __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
   if constexpr (C == 8) {
@@ -118,14 +131,20 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 //              BF16 value) before the MMAs read the stage; the scale folds into the weight,
 //              nu' = nu s^d: with z = q^T a, the terms of eq. Y and Lemma 3.5 are nu' z^{d-1} q
 //              and nu' z^d.
-// RRF = true:  the randomized range finder of eq. rrf, Y_part = sum_l v_l omega_l^T: no MMA1 and
-//              no w; the epilogue draws row l of the Gaussian test matrix (Philox4x32-10, FP32
-//              Box-Muller; times s_l for E4M3) as W, and MMA2 accumulates V^T W as above. MMA2
-//              then waits for the staged tile itself, which MMA1 otherwise orders.
-template <int RP, bool FP8, bool RRF>
-__global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
+// MODE = kRrf:    the randomized range finder of eq. rrf, Y_part = sum_l v_l omega_l^T: no MMA1
+//                 and no w; the epilogue draws row l of the Gaussian test matrix (Philox4x32-10,
+//                 FP32 Box-Muller; times s_l for E4M3) as W, and MMA2 accumulates V^T W as above.
+//                 MMA2 then waits for the staged tile itself, which MMA1 otherwise orders.
+// MODE = kGather: the sampled evaluation of Sec. 5 (Lemma 5.1) on rows idx[0..p) of BF16
+//                 samples: NCONV gather warps copy the rows into the stages in place of TMA.
+enum PassMode { kFused = 0, kRrf = 1, kGather = 2 };
+
+template <int RP, bool FP8, int MODE>
+__global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
-  constexpr int NT = FP8 ? NTHREADS_FP8 : NTHREADS;
+  constexpr bool RRF = MODE == kRrf, GATHER = MODE == kGather;
+  static_assert(!(GATHER && FP8), "gathered rows: BF16 samples");
+  constexpr int NT = (FP8 || GATHER) ? NTHREADS_FP8 : NTHREADS;
   using C = Cfg<RP>;
   constexpr int N = C::N;
   if (prm.skip && *prm.skip) return;
@@ -160,7 +179,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&full[s], GATHER ? NCONV : 1);  // TMA, or one arrival per gather warp
       tc::mbar_init(&empty[s], 1);
       tc::mbar_init(&conv[s], NCONV);  // one arrival per converter warp
     }
@@ -177,7 +196,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
+  if (!GATHER && warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
   if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
 
   // A split: the hi row of component j holds BF16(a_j), its lo row BF16(a_j - BF16(a_j)); K =
@@ -222,7 +241,7 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
-    if (lane == 0) {
+    if (!GATHER && lane == 0) {
       // BF16: tiles go straight to the MMAs; E4M3: the converters widen them in place first
       const int R = S;
       uint64_t* rfull = full;
@@ -326,6 +345,72 @@ __global__ void __launch_bounds__(FP8 ? NTHREADS_FP8 : NTHREADS, 1)
       if (!ok) fail();
       tc::mma_commit(&mma_done[1]);
       tc::mbar_wait(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
+    }
+  } else if (GATHER && warp >= 3 + NEPI / 32) {
+    // ------------------------------------------------------------------ row gather (Sec. 5)
+    // Gather warp G copies rows y = G + 4k (k = 0..31) of tile t: row y is sample idx[t TM + y],
+    // and one warp instruction copies the whole row, lane l taking its 16-byte chunk l (features
+    // 8l .. 8l + 7: region l / 8, chunk l % 8 at position (l % 8) ^ (y & 7) of the 128-byte
+    // swizzle TMA would use), so each instruction reads whole 128-byte lines. Features past n and
+    // rows past p are zero-filled; a row outside the storage reads as zero and sets STMF_EINVAL.
+    // cp.async writes through the generic proxy, so each thread waits for its own copies and
+    // fences them to the async proxy (the MMAs) before its warp arrives; two tiles are in flight
+    // per warp, and the row indices are read one tile ahead (one per lane).
+    if constexpr (GATHER) {
+      const int G = warp - (3 + NEPI / 32);  // 0 .. NCONV - 1
+      const uint16_t* Vg = static_cast<const uint16_t*>(prm.V);
+      const int lg = lane >> 3, lc = lane & 7;  // this lane's region and chunk of a row
+      const int f0 = 64 * lg + 8 * lc;          // its first feature
+      const int valid = n - f0 >= 8 ? 8 : (n - f0 > 0 ? n - f0 : 0);
+      const bool active = lg < nload;           // regions past the last loaded one stay zero
+      auto row_of = [&](int it_) -> int64_t {   // the row of sample y = G + 4 lane of tile it_
+        const int64_t pos = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + G + 4 * lane;
+        if (it_ >= my_tiles || pos >= prm.p) return -1;
+        const int64_t row = prm.idx[pos];
+        if (row < 0 || row >= prm.rows) {
+          stmf_set_status(prm.status, STMF_EINVAL);
+          return -1;
+        }
+        return row;
+      };
+      auto retire = [&](int k) {  // this warp's copies of tile k have landed
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full[k % S]);
+      };
+      bool ok = true;
+      int64_t row_next = row_of(0);
+      int it = 0;
+      for (; it < my_tiles; ++it) {
+        const int st = it % S;
+        ok = tc::mbar_wait(&empty[st], ((it / S) & 1) ^ 1, abortv, WAIT_LIMIT);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        const int64_t my_row = row_next;  // row of sample G + 4 lane
+        row_next = row_of(it + 1);
+        const uint32_t stage0 = tc::smem_addr(sV + size_t(st) * stage_bytes) +
+                                uint32_t(lg) * REG_BYTES;
+        for (int k = 0; k < 32; ++k) {
+          const int y = G + 4 * k;
+          const int64_t row = __shfl_sync(0xffffffffu, my_row, k);
+          if (active) {
+            const int nb = row < 0 ? 0 : valid;
+            const uint16_t* src = nb ? Vg + row * prm.ld + f0 : Vg;
+            cp_async16(stage0 + uint32_t(y) * 128u + ((uint32_t(lc) ^ uint32_t(y & 7)) << 4), src,
+                       uint32_t(2 * nb));
+          }
+        }
+        cp_async_commit();
+        if (it >= 1) {
+          cp_async_wait<1>();
+          retire(it - 1);
+        }
+      }
+      cp_async_wait<0>();  // nothing of this thread's stays in flight past here
+      if (ok && it >= 1) retire(it - 1);
+      if (!ok) fail();
     }
   } else if (FP8 && warp >= 3 + NEPI / 32) {
     // ------------------------------------------------------------------ E4M3 -> BF16 converters
@@ -627,14 +712,14 @@ TcExtra plan(int n, int r, bool) {  // the same staging serves BF16 and E4M3 sam
   return ex;
 }
 
-template <int RP, bool FP8, bool RRF>
+template <int RP, bool FP8, int MODE>
 cudaError_t launch_rp(const CUtensorMap& tmap, const FgParams& prm, const TcExtra& ex, int grid,
                       cudaStream_t s) {
-  const cudaError_t e = smem_limit((const void*)fg_tc_kernel<RP, FP8, RRF>, 232448);
+  const cudaError_t e = smem_limit((const void*)fg_tc_kernel<RP, FP8, MODE>, 232448);
   if (e != cudaSuccess) return e;
-  return launch_kernel(fg_tc_kernel<RP, FP8, RRF>, dim3(grid),
-                       dim3(FP8 ? NTHREADS_FP8 : NTHREADS), size_t(ex.smem_bytes), s, tmap, prm,
-                       ex);
+  return launch_kernel(fg_tc_kernel<RP, FP8, MODE>, dim3(grid),
+                       dim3((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHREADS),
+                       size_t(ex.smem_bytes), s, tmap, prm, ex);
 }
 
 }  // namespace
@@ -659,15 +744,17 @@ int fg_tc_grid(int, int, int, int64_t p, int num_sms, int min_tiles) {
 
 namespace {
 
-template <bool RRF>
+template <int MODE>
 cudaError_t launch_tc(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
   if (dtype != STMF_BF16 && dtype != STMF_E4M3) return cudaErrorNotSupported;
+  if (MODE == kGather && (dtype != STMF_BF16 || !prm.idx)) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
   EncodeFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   const bool fp8 = dtype == STMF_E4M3;
   CUtensorMap tmap;
-  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
+  // (gathered rows: the map spans the whole storage and goes unused)
+  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)(MODE == kGather ? prm.rows : prm.p)};
   const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * (fp8 ? 1 : 2)};
   const cuuint32_t box[2] = {fp8 ? 128u : 64u, TM};  // 128-byte rows either way
   const cuuint32_t estr[2] = {1, 1};
@@ -677,22 +764,28 @@ cudaError_t launch_tc(int dtype, const FgParams& prm, int grid, cudaStream_t s) 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const TcExtra ex = plan(prm.n, prm.r, fp8);
-  if (fp8) {
-    if (rp_of(prm.r) == 8) return launch_rp<8, true, RRF>(tmap, prm, ex, grid, s);
-    return launch_rp<16, true, RRF>(tmap, prm, ex, grid, s);
+  if constexpr (MODE != kGather) {
+    if (fp8) {
+      if (rp_of(prm.r) == 8) return launch_rp<8, true, MODE>(tmap, prm, ex, grid, s);
+      return launch_rp<16, true, MODE>(tmap, prm, ex, grid, s);
+    }
   }
-  if (rp_of(prm.r) == 8) return launch_rp<8, false, RRF>(tmap, prm, ex, grid, s);
-  return launch_rp<16, false, RRF>(tmap, prm, ex, grid, s);
+  if (rp_of(prm.r) == 8) return launch_rp<8, false, MODE>(tmap, prm, ex, grid, s);
+  return launch_rp<16, false, MODE>(tmap, prm, ex, grid, s);
 }
 
 }  // namespace
 
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
-  return launch_tc<false>(dtype, prm, grid, s);
+  return launch_tc<kFused>(dtype, prm, grid, s);
 }
 
 cudaError_t fg_tc_rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
-  return launch_tc<true>(dtype, prm, grid, s);
+  return launch_tc<kRrf>(dtype, prm, grid, s);
+}
+
+cudaError_t fg_tc_gather_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_tc<kGather>(dtype, prm, grid, s);
 }
 
 }  // namespace stmf

@@ -119,6 +119,8 @@ int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms, int min_tiles = 
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 // the range finder of eq. rrf on the same pass (Y partials of V Omega, w = 0; prm.seed)
 cudaError_t fg_tc_rrf_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+// the sampled evaluation of Sec. 5 on the same pass: rows prm.idx[0..p) of BF16 samples
+cudaError_t fg_tc_gather_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 cudaError_t model_terms_launch(const ModelParams& prm, cudaStream_t s);
 int gram_simt_grid(int dtype, int n, int64_t p, int num_sms);
 bool gram_tc_supported(int dtype, int n, int64_t p);
@@ -140,7 +142,7 @@ cudaError_t norm_sym_launch(int dtype, const SymParams& prm, dim3 grid, cudaStre
 // tensor-core pass for BF16/E4M3 with n <= 256, the sub-stage tensor-core pass for FP32 with
 // n <= 256 and for BF16/E4M3 with n <= 512, else the register-blocked FP32 pass (FP32, r <= 16),
 // else the CUDA-core pass. Gathered rows (an index array) take the CUDA-core passes only.
-enum PassKind { kPassTc = 0, kPassTcSub = 1, kPassF32 = 2, kPassSimt = 3 };
+enum PassKind { kPassTc = 0, kPassTcSub = 1, kPassF32 = 2, kPassSimt = 3, kPassTcGather = 4 };
 struct PassPlan {
   PassKind kind;
   int grid;

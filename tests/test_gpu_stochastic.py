@@ -58,6 +58,41 @@ def test_fg_sampled_out_of_range_index_is_reported(stmf):
     assert stmf.default_context().device_status() == 1   # STMF_EINVAL
 
 
+@pytest.mark.parametrize("n,s,r", [(256, 30001, 16), (100, 5000, 10), (37, 129, 3)])
+def test_fg_sampled_tensor_cores(stmf, n, s, r):
+    """BF16 rows gathered by the tensor-core pass (warps copy the sampled rows into its stages):
+    several tiles and a ragged last one, n = 100 and 37 ending inside a 16-byte chunk, rows
+    drawn with repeats; against the oracle on the BF16 values, normwise and entry by entry."""
+    p, d = 60000, 4
+    data = inputs.gmm(n, p, 8, 0.1, seed=n + s)
+    st = inputs.to_storage(data["V"], "bf16", device="cuda")
+    Vd = formats.decode_bf16(inputs.storage_bits(st))
+    idx = np.random.default_rng(s).integers(0, p, size=s)
+    lam, A = inputs.random_model(n, r, seed=s)
+    f_ref, gl_ref, GA_ref = stochastic.fg_sampled(Vd.T, idx, lam, A, d)
+    f, gl, GA = stmf.fg_sampled(st, torch.tensor(idx, device="cuda"), d,
+                                torch.tensor(lam, device="cuda"),
+                                torch.tensor(A.T.copy(), device="cuda").T)
+    torch.cuda.synchronize()
+    assert stmf.default_context().device_status() == 0
+    tol = TOL["bf16"]
+    assert abs(f.item() - f_ref) <= tol * max(abs(f_ref), np.abs(gl_ref).max())
+    gl_h, GA_h = gl.cpu().numpy(), GA.cpu().numpy()
+    assert rel(gl_h, gl_ref) <= tol and rel(GA_h, GA_ref) <= tol
+    assert np.max(np.abs(GA_h - GA_ref)) <= 10 * tol * np.max(np.abs(GA_ref))
+
+
+def test_fg_sampled_tensor_cores_out_of_range_index(stmf):
+    """A sampled BF16 row outside the storage reads as zero and is reported (STMF_EINVAL)."""
+    st = inputs.to_storage(np.ones((300, 64)), "bf16", device="cuda")
+    idx = torch.tensor([0, 5, 300, 7], device="cuda")   # 300 is outside [0, p)
+    f, _, _ = stmf.fg_sampled(st, idx, 3, torch.ones(2, dtype=torch.float64, device="cuda"),
+                              torch.ones((2, 64), dtype=torch.float64, device="cuda").T)
+    torch.cuda.synchronize()
+    assert stmf.default_context().device_status() == 1   # STMF_EINVAL
+    assert np.isfinite(f.item())
+
+
 def test_adam_matches_oracle_schedule(stmf):
     """FP64 samples: the device Adam takes the oracle's steps (same sampled rows), through the
     learning-rate drop and the stop."""
