@@ -207,16 +207,32 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// 16-byte global -> shared copy of which the first `bytes` are read (the rest zero-filled).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void epi_barrier() {
   asm volatile("bar.sync 1, %0;" ::"n"(NEPI) : "memory");
 }
 
 // NS: sub-stages per tile the epilogue keeps Y sums for (1, 2 or 4; at least ex.nsub).
 // MODE: the storage type of the samples (SubMode).
-template <int RP, int NS, int MODE>
+// GATHER: sampled FP32 rows idx[0..p) (Sec. 5, Lemma 5.1), fetched by the converter warps in
+//         place of TMA.
+template <int RP, int NS, int MODE, bool GATHER>
 __global__ void __launch_bounds__(NTHREADS, 1)
     fg_tc_sub_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm,
                      const SubExtra ex) {
+  static_assert(!GATHER || MODE == kF32, "gathered rows: FP32 samples");
   constexpr int FS = feats_per_sub(MODE);  // features per sub-stage
   constexpr int AR = FS / 64;              // A-split regions per sub-stage
   constexpr bool CONVERT = MODE != kBF16;  // converter warps rewrite each sub-stage
@@ -278,7 +294,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
+  if (!GATHER && warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
   if (warp == 1) tc::tmem_alloc(tmem_slot, ex.tmem_cols);
 
   // A split: row k RP + j holds term k of a_j, with A1 = BF16(a), A2 = BF16(a - A1),
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
-    if (lane == 0) {
+    if (!GATHER && lane == 0) {
       int issued = 0;
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
@@ -463,7 +479,95 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if constexpr (CONVERT) {
       const int y = tid - CONV0;
       const uint32_t sw = uint32_t(y & 7);
+      // FP32: row y of both regions of sub-stage `slot`, split in place
+      auto split_row = [&](int slot) {
+        unsigned char* row0 = sV + size_t(slot) * SUB_BYTES + y * 128;
+#pragma unroll 1
+        for (int rg = 0; rg < 2; ++rg) {
+          unsigned char* row = row0 + size_t(rg) * REG_BYTES;
+          float x[8][4];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 a = *reinterpret_cast<const float4*>(row + ((c ^ sw) << 4));
+            x[c][0] = a.x; x[c][1] = a.y; x[c][2] = a.z; x[c][3] = a.w;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {  // features 8k .. 8k + 7 of the region
+            const float v[8] = {x[2 * k][0],     x[2 * k][1],     x[2 * k][2],
+                                x[2 * k][3],     x[2 * k + 1][0], x[2 * k + 1][1],
+                                x[2 * k + 1][2], x[2 * k + 1][3]};
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
+            *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
+          }
+        }
+      };
       bool ok = true;
+      if constexpr (GATHER) {
+        // Sampled FP32 rows (Sec. 5): the converter warps fetch the rows themselves. Warp w
+        // holds rows y = 32 w + l of every tile (lane l: the row index of sample y, read one
+        // tile ahead); one warp instruction copies the sub-stage's 256-byte slices of two rows
+        // (lanes 0-15 and 16-31, 16-byte chunk q = features 4q .. 4q + 3 of the sub-stage:
+        // region q / 8, chunk q % 8 at position (q % 8) ^ (y & 7) of the 128-byte swizzle).
+        // Features past n and rows past p are zero-filled; a row outside the storage reads as
+        // zero and sets STMF_EINVAL. Sub-stage k + 1 is requested before sub-stage k is split:
+        // each thread waits for its own copies of k, the warp syncs (its rows are complete),
+        // every thread splits its row, fences to the async proxy, and the warp arrives.
+        const int w = y >> 5, half = lane >> 4, q = lane & 15;
+        const float* Vg = static_cast<const float*>(prm.V);
+        auto row_of = [&](int it_) -> int64_t {
+          const int64_t pos = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + y;
+          if (it_ >= my_tiles || pos >= prm.p) return -1;
+          const int64_t row = prm.idx[pos];
+          if (row < 0 || row >= prm.rows) {
+            stmf_set_status(prm.status, STMF_EINVAL);
+            return -1;
+          }
+          return row;
+        };
+        auto finish = [&](int seq_) {
+          __syncwarp();
+          split_row(seq_ % R);
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&conv[seq_ % R]);
+        };
+        int64_t row_cur = -1, row_next = row_of(0);
+        int seq = 0;
+        for (int it = 0; it < my_tiles && ok; ++it) {
+          row_cur = row_next;
+          row_next = row_of(it + 1);
+          for (int h = 0; h < nsub; ++h, ++seq) {
+            const int slot = seq % R;
+            ok = tc::mbar_wait_sleep(&empty[slot], ((seq / R) & 1) ^ 1, abortv, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, ok)) {
+              ok = false;
+              break;
+            }
+            const uint32_t base = tc::smem_addr(sV + size_t(slot) * SUB_BYTES);
+            const int f = FS * h + 4 * q;
+            const int fv = n - f >= 4 ? 4 : (n - f > 0 ? n - f : 0);
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+              const int yy = 32 * w + 2 * i + half;
+              const int64_t row = __shfl_sync(0xffffffffu, row_cur, 2 * i + half);
+              const int nb = row < 0 ? 0 : fv;
+              const float* src = nb ? Vg + row * prm.ld + f : Vg;
+              cp_async16(base + uint32_t(q >> 3) * REG_BYTES + uint32_t(yy) * 128u +
+                             ((uint32_t(q & 7) ^ uint32_t(yy & 7)) << 4),
+                         src, uint32_t(4 * nb));
+            }
+            cp_async_commit();
+            if (seq >= 1) {
+              cp_async_wait<1>();
+              finish(seq - 1);
+            }
+          }
+        }
+        cp_async_wait<0>();  // nothing of this thread's stays in flight past here
+        if (ok && seq >= 1) finish(seq - 1);
+      } else {
       int seq = 0;
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int h = 0; h < nsub; ++h, ++seq) {
@@ -473,29 +577,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = false;
             break;
           }
-          unsigned char* row0 = sV + size_t(slot) * SUB_BYTES + y * 128;
           if constexpr (MODE == kF32) {
-#pragma unroll 1
-            for (int rg = 0; rg < 2; ++rg) {
-              unsigned char* row = row0 + size_t(rg) * REG_BYTES;
-              float x[8][4];
-#pragma unroll
-              for (int c = 0; c < 8; ++c) {
-                const float4 a = *reinterpret_cast<const float4*>(row + ((c ^ sw) << 4));
-                x[c][0] = a.x; x[c][1] = a.y; x[c][2] = a.z; x[c][3] = a.w;
-              }
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {  // features 8k .. 8k + 7 of the region
-                const float v[8] = {x[2 * k][0],     x[2 * k][1],     x[2 * k][2],
-                                    x[2 * k][3],     x[2 * k + 1][0], x[2 * k + 1][1],
-                                    x[2 * k + 1][2], x[2 * k + 1][3]};
-                uint4 hi, lo;
-                split8(v, hi, lo);
-                *reinterpret_cast<uint4*>(row + ((uint32_t(k) ^ sw) << 4)) = hi;
-                *reinterpret_cast<uint4*>(row + ((uint32_t(4 + k) ^ sw) << 4)) = lo;
-              }
-            }
+            split_row(slot);
           } else {
+            unsigned char* row0 = sV + size_t(slot) * SUB_BYTES + y * 128;
             unsigned char* row1 = row0 + REG_BYTES;
             const unsigned char* src = sRaw + size_t(fs) * REG_BYTES + y * 128;
             uint4 raw[8];
@@ -528,6 +613,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&conv[slot]);
         }
+      }
       }
       if (!ok) fail();
     }
@@ -788,28 +874,29 @@ SubExtra plan_sub(int mode, int n, int r) {
   return ex;
 }
 
-template <int RP, int NS, int MODE>
+template <int RP, int NS, int MODE, bool GATHER>
 cudaError_t launch_sub(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex, int grid,
                        cudaStream_t s) {
-  const cudaError_t e = smem_limit((const void*)fg_tc_sub_kernel<RP, NS, MODE>, (int)kMaxSmem);
+  const cudaError_t e =
+      smem_limit((const void*)fg_tc_sub_kernel<RP, NS, MODE, GATHER>, (int)kMaxSmem);
   if (e != cudaSuccess) return e;
-  return launch_kernel(fg_tc_sub_kernel<RP, NS, MODE>, dim3(grid), dim3(NTHREADS),
+  return launch_kernel(fg_tc_sub_kernel<RP, NS, MODE, GATHER>, dim3(grid), dim3(NTHREADS),
                        size_t(ex.smem_bytes), s, tmap, prm, ex);
 }
 
-template <int RP, int MODE>
+template <int RP, int MODE, bool GATHER>
 cudaError_t launch_sub_ns(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex,
                           int grid, cudaStream_t s) {
-  if (ex.nsub == 1) return launch_sub<RP, 1, MODE>(tmap, prm, ex, grid, s);
-  if (ex.nsub == 2) return launch_sub<RP, 2, MODE>(tmap, prm, ex, grid, s);
-  return launch_sub<RP, 4, MODE>(tmap, prm, ex, grid, s);
+  if (ex.nsub == 1) return launch_sub<RP, 1, MODE, GATHER>(tmap, prm, ex, grid, s);
+  if (ex.nsub == 2) return launch_sub<RP, 2, MODE, GATHER>(tmap, prm, ex, grid, s);
+  return launch_sub<RP, 4, MODE, GATHER>(tmap, prm, ex, grid, s);
 }
 
-template <int MODE>
+template <int MODE, bool GATHER>
 cudaError_t launch_sub_rp(const CUtensorMap& tmap, const FgParams& prm, const SubExtra& ex,
                           int grid, cudaStream_t s) {
-  if (rp_of(prm.r) == 8) return launch_sub_ns<8, MODE>(tmap, prm, ex, grid, s);
-  return launch_sub_ns<16, MODE>(tmap, prm, ex, grid, s);
+  if (rp_of(prm.r) == 8) return launch_sub_ns<8, MODE, GATHER>(tmap, prm, ex, grid, s);
+  return launch_sub_ns<16, MODE, GATHER>(tmap, prm, ex, grid, s);
 }
 
 }  // namespace
@@ -834,15 +921,20 @@ int fg_tc_sub_grid(int64_t p, int num_sms, int min_tiles) {
   return (int)(want < num_sms ? want : num_sms);
 }
 
-cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+namespace {
+
+template <bool GATHER>
+cudaError_t launch_any(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
   const int mode = mode_of(dtype);
   if (mode < 0) return cudaErrorNotSupported;
+  if (GATHER && (mode != kF32 || !prm.idx)) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
   EncodeFn enc = get_encode_sub();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmap;
   const int eb = mode == kF32 ? 4 : mode == kBF16 ? 2 : 1;
-  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)prm.p};
+  // (gathered rows: the map spans the whole storage and goes unused)
+  const cuuint64_t dims[2] = {(cuuint64_t)prm.n, (cuuint64_t)(GATHER ? prm.rows : prm.p)};
   const cuuint64_t strides[1] = {(cuuint64_t)prm.ld * eb};
   const cuuint32_t box[2] = {128u / eb, TM};  // 128-byte rows
   const cuuint32_t estr[2] = {1, 1};
@@ -854,9 +946,32 @@ cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStrea
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const SubExtra ex = plan_sub(mode, prm.n, prm.r);
-  if (mode == kF32) return launch_sub_rp<kF32>(tmap, prm, ex, grid, s);
-  if (mode == kBF16) return launch_sub_rp<kBF16>(tmap, prm, ex, grid, s);
-  return launch_sub_rp<kE4M3>(tmap, prm, ex, grid, s);
+  if constexpr (GATHER) {
+    // the converters finish sub-stage k after requesting k + 1, which needs the ring to hold a
+    // whole tile beyond it
+    if (ex.ring < ex.nsub + 1) return cudaErrorNotSupported;
+    return launch_sub_rp<kF32, true>(tmap, prm, ex, grid, s);
+  } else {
+    if (mode == kF32) return launch_sub_rp<kF32, false>(tmap, prm, ex, grid, s);
+    if (mode == kBF16) return launch_sub_rp<kBF16, false>(tmap, prm, ex, grid, s);
+    return launch_sub_rp<kE4M3, false>(tmap, prm, ex, grid, s);
+  }
+}
+
+}  // namespace
+
+cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_any<false>(dtype, prm, grid, s);
+}
+
+cudaError_t fg_tc_sub_gather_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
+  return launch_any<true>(dtype, prm, grid, s);
+}
+
+bool fg_tc_sub_gather_supported(int dtype, int n, int r) {
+  if (dtype != STMF_F32 || !fg_tc_sub_supported(dtype, n, r)) return false;
+  const SubExtra ex = plan_sub(kF32, n, r);
+  return ex.ring >= ex.nsub + 1;
 }
 
 }  // namespace stmf

@@ -99,6 +99,9 @@ bool stmf::plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gathe
   if (gather && dtype == STMF_BF16 && fg_tc_supported(dtype, n, r)) {
     // sampled BF16 rows: the tensor-core pass with warps gathering the rows in place of TMA
     pl = {kPassTcGather, fg_tc_grid(dtype, n, r, p, num_sms, min_tiles)};
+  } else if (gather && fg_tc_sub_gather_supported(dtype, n, r)) {
+    // sampled FP32 rows: the sub-stage pass, its converter warps fetching the rows
+    pl = {kPassTcSubGather, fg_tc_sub_grid(p, num_sms, min_tiles)};
   } else if (!gather && fg_tc_supported(dtype, n, r)) {
     pl = {kPassTc, fg_tc_grid(dtype, n, r, p, num_sms, min_tiles)};
   } else if (!gather && fg_tc_sub_supported(dtype, n, r)) {
@@ -117,6 +120,7 @@ cudaError_t stmf::launch_pass(const stmf::PassPlan& pl, int dtype, const stmf::F
   switch (pl.kind) {
     case kPassTc: return fg_tc_launch(dtype, prm, pl.grid, s);
     case kPassTcGather: return fg_tc_gather_launch(dtype, prm, pl.grid, s);
+    case kPassTcSubGather: return fg_tc_sub_gather_launch(dtype, prm, pl.grid, s);
     case kPassTcSub: return fg_tc_sub_launch(dtype, prm, pl.grid, s);
     case kPassF32: return fg_f32_launch(prm, pl.grid, s);
     default: return fg_simt_launch(dtype, prm, pl.grid, s);

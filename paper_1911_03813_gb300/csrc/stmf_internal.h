@@ -114,6 +114,9 @@ cudaError_t fg_f32_launch(const FgParams& prm, int grid, cudaStream_t s);
 bool fg_tc_sub_supported(int dtype, int n, int r);
 int fg_tc_sub_grid(int64_t p, int num_sms, int min_tiles = 1);
 cudaError_t fg_tc_sub_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
+// the sampled evaluation of Sec. 5 on the sub-stage pass: rows prm.idx[0..p) of FP32 samples
+bool fg_tc_sub_gather_supported(int dtype, int n, int r);
+cudaError_t fg_tc_sub_gather_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
 size_t fg_tc_supported(int dtype, int n, int r);  // nonzero when the tensor-core pass applies
 int fg_tc_grid(int dtype, int n, int r, int64_t p, int num_sms, int min_tiles = 1);
 cudaError_t fg_tc_launch(int dtype, const FgParams& prm, int grid, cudaStream_t s);
@@ -142,7 +145,9 @@ cudaError_t norm_sym_launch(int dtype, const SymParams& prm, dim3 grid, cudaStre
 // tensor-core pass for BF16/E4M3 with n <= 256, the sub-stage tensor-core pass for FP32 with
 // n <= 256 and for BF16/E4M3 with n <= 512, else the register-blocked FP32 pass (FP32, r <= 16),
 // else the CUDA-core pass. Gathered rows (an index array) take the CUDA-core passes only.
-enum PassKind { kPassTc = 0, kPassTcSub = 1, kPassF32 = 2, kPassSimt = 3, kPassTcGather = 4 };
+enum PassKind {
+  kPassTc = 0, kPassTcSub = 1, kPassF32 = 2, kPassSimt = 3, kPassTcGather = 4, kPassTcSubGather = 5
+};
 struct PassPlan {
   PassKind kind;
   int grid;

@@ -58,15 +58,18 @@ def test_fg_sampled_out_of_range_index_is_reported(stmf):
     assert stmf.default_context().device_status() == 1   # STMF_EINVAL
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
 @pytest.mark.parametrize("n,s,r", [(256, 30001, 16), (100, 5000, 10), (37, 129, 3)])
-def test_fg_sampled_tensor_cores(stmf, n, s, r):
-    """BF16 rows gathered by the tensor-core pass (warps copy the sampled rows into its stages):
-    several tiles and a ragged last one, n = 100 and 37 ending inside a 16-byte chunk, rows
-    drawn with repeats; against the oracle on the BF16 values, normwise and entry by entry."""
+def test_fg_sampled_tensor_cores(stmf, dtype, n, s, r):
+    """Rows gathered by the tensor-core passes (BF16: gather warps of the whole-tile pass; FP32:
+    the converter warps of the sub-stage pass fetch the rows before splitting them): several
+    tiles and a ragged last one, n = 100 and 37 ending inside a 16-byte chunk, rows drawn with
+    repeats; against the oracle on the stored values, normwise and entry by entry."""
     p, d = 60000, 4
     data = inputs.gmm(n, p, 8, 0.1, seed=n + s)
-    st = inputs.to_storage(data["V"], "bf16", device="cuda")
-    Vd = formats.decode_bf16(inputs.storage_bits(st))
+    st = inputs.to_storage(data["V"], dtype, device="cuda")
+    bits = inputs.storage_bits(st)
+    Vd = formats.decode_bf16(bits) if dtype == "bf16" else np.asarray(bits, dtype=np.float64)
     idx = np.random.default_rng(s).integers(0, p, size=s)
     lam, A = inputs.random_model(n, r, seed=s)
     f_ref, gl_ref, GA_ref = stochastic.fg_sampled(Vd.T, idx, lam, A, d)
@@ -75,7 +78,7 @@ def test_fg_sampled_tensor_cores(stmf, n, s, r):
                                 torch.tensor(A.T.copy(), device="cuda").T)
     torch.cuda.synchronize()
     assert stmf.default_context().device_status() == 0
-    tol = TOL["bf16"]
+    tol = TOL[dtype]
     assert abs(f.item() - f_ref) <= tol * max(abs(f_ref), np.abs(gl_ref).max())
     gl_h, GA_h = gl.cpu().numpy(), GA.cpu().numpy()
     assert rel(gl_h, gl_ref) <= tol and rel(GA_h, GA_ref) <= tol
