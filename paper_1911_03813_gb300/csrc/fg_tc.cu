@@ -1,4 +1,7 @@
-// Fused pass over BF16 samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM).
+// Fused pass over BF16 (and E4M3) samples on the 5th-generation tensor cores (tcgen05, TMA,
+// TMEM), with two more modes of the same pipeline: the randomized range finder of eq. rrf
+// (A0 = V Omega, Omega drawn in the epilogue, no MMA1) and the sampled evaluation of Sec. 5
+// (rows idx[0..p) copied into the stages by gather warps in place of TMA).
 //
 // Computes, per persistent CTA and over that CTA's sample tiles, the partial sums of Alg. 2's
 // Y (Lemma 3.3, eq. Y) and of Lemma 3.5:
@@ -18,7 +21,8 @@
 //
 // Warp roles (608 threads): warp 0 = TMA producer, warp 1 = TMEM allocator and MMA1 issuer,
 // warp 2 = MMA2 issuer, warps 3-18 = epilogue in four warpgroups that split the components
-// (thread = TMEM lane = sample of the tile, or feature of the M-block).
+// (thread = TMEM lane = sample of the tile, or feature of the M-block); E4M3 samples add warps
+// 19-22 that widen the codes, gathered rows add warps 19-22 that copy the rows (736 threads).
 // Pipelines: S shared-memory stages of V; double-buffered Z (TMEM) and W (shared memory); Y
 // accumulates in TMEM and is folded into compensated FP32 registers every `flush` tiles (FP64
 // from the block partials on), with two TMEM

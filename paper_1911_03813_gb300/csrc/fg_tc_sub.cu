@@ -1,6 +1,7 @@
 // Fused pass over samples on the 5th-generation tensor cores (tcgen05, TMA, TMEM), streaming
 // each tile through a ring of sub-stages: FP32 samples (n <= 256), and BF16 or E4M3 samples with
-// more features than the whole-tile pass holds (n <= 512).
+// more features than the whole-tile pass holds (n <= 512). For the sampled evaluation of Sec. 5
+// on FP32 rows idx[0..p), the converter warps copy the rows into the sub-stages themselves.
 //
 // Computes the same per-CTA partial sums of Alg. 2 as the whole-tile pass (Lemma 3.3, eq. Y;
 // Lemma 3.5):
