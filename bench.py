@@ -421,6 +421,65 @@ def other_passes_bench(st16, st32, lam_t, A_t, dev):
     return out
 
 
+# Sec. 4.1's timing scenarios (Table timing_compare): d, n, p, r and the paper's implicit time per
+# inner iteration in seconds (MATLAB on a 28-core CPU; context, not a target)
+PAPER_E1 = [(3, 75, 750, 5, 4.36e-4), (3, 75, 750, 25, 5.91e-4), (3, 75, 3750, 5, 7.96e-4),
+            (3, 75, 3750, 25, 1.03e-3), (3, 375, 3750, 5, 4.82e-3), (4, 75, 3750, 5, 9.22e-4)]
+
+
+def paper_shapes_bench(dev, oracle_seconds=1.0):
+    """Sec. 4.1's six timing scenarios as a context workload: uniform(0,1) samples in FP64. Per
+    scenario: the device's time per f+grad evaluation (200 back to back, CUDA events); a fit on
+    the device from a seeded random start with pgtol = 0.05, as in Sec. 4.1 (time per inner
+    iteration, the paper's unit); the FP64 oracle's time per evaluation on the host cores; and
+    the paper's implicit time per inner iteration beside them."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1911_03813_gb300 import inputs, stmf
+    rows = []
+    for k, (d, n, p, r, paper_s) in enumerate(PAPER_E1):
+        V = inputs.uniform(n, p, seed=SEED + k)
+        st = inputs.to_storage(V, "f64", device=dev)
+        lam, A = inputs.random_model(n, r, seed=SEED + 100 + k)
+        lam_t = torch.tensor(lam, device=dev)
+        A_t = torch.tensor(np.ascontiguousarray(A.T), device=dev).T
+        out = (torch.empty(1, dtype=torch.float64, device=dev),
+               torch.empty(r, dtype=torch.float64, device=dev),
+               torch.empty((r, n), dtype=torch.float64, device=dev).T)
+        for _ in range(5):
+            stmf.fg(st, None, d, lam_t, A_t, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            stmf.fg(st, None, d, lam_t, A_t, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        eval_s = e0.elapsed_time(e1) / 200 / 1e3
+        lam_f = lam_t.clone()
+        A_f = torch.tensor(np.ascontiguousarray(A.T), device=dev).T  # column-major, updated in place
+        t0 = time.perf_counter()
+        res = stmf.fit(st, None, d, lam_f, A_f, pgtol=0.05, max_evals=50000)
+        fit_s = time.perf_counter() - t0
+        Vt = np.ascontiguousarray(V.T)
+        t0, ko = time.perf_counter(), 0
+        while time.perf_counter() - t0 < oracle_seconds:
+            oracle.fg_implicit(None, Vt, lam, A, d)
+            ko += 1
+        oracle_s = (time.perf_counter() - t0) / ko
+        rows.append({"d": d, "n": n, "p": p, "r": r, "gpu_s_per_eval": eval_s,
+                     "gpu_fit_s": fit_s, "gpu_fit_evals": res["evals"],
+                     "gpu_fit_s_per_iter": fit_s / max(res["evals"], 1),
+                     "fit_stop": res["stop_name"], "oracle_s_per_eval": oracle_s,
+                     "paper_implicit_s_per_iter": paper_s})
+    return {"workload": "Sec. 4.1 scenarios, uniform(0,1) samples, FP64, nu = 1/p",
+            "paper_context": "Table timing_compare, implicit method: MATLAB 2018a on 2 x Intel "
+                             "E5-2683 (28 cores), L-BFGS-B; per inner iteration",
+            "oracle_cores": len(os.sched_getaffinity(0)), "scenarios": rows}
+
+
 def gram_bench(dev):
     """One ||X||^2 Gram pass (tensor cores, BF16) on the first 2^18 samples of the workload (the
     pass is O(p^2 n): 1.8e13 FLOP here; with 2^16 samples, about 14 work items per CTA, the tail
@@ -636,6 +695,8 @@ def main():
                     help="run the Gaussian-mixture study grid of Sec. 4.2 (n=500) and print its line")
     ap.add_argument("--alpha-only", action="store_true",
                     help="only ||X||^2 from the distinct entries of X at n=100, p=2.5e6, d=3")
+    ap.add_argument("--paper-shapes-only", action="store_true",
+                    help="time only Sec. 4.1's six scenarios (FP64) and print them")
     ap.add_argument("--gram-only", action="store_true",
                     help="time only the ||X||^2 Gram pass on 2^18 samples and print it")
     ap.add_argument("--legs", default="bf16,fp32,fp8",
@@ -659,6 +720,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.paper_shapes_only:
+        print(json.dumps(paper_shapes_bench(dev)), flush=True)
+        return
     if args.gram_only:
         print(json.dumps(gram_bench(dev)), flush=True)
         return
@@ -817,6 +881,7 @@ def main():
     alpha = None if args.no_gram else alpha_bench(dev)
     fp32_scale = None if args.no_gram else fp32_scale_bench(dev)
     differentiation = None if args.no_gram else autograd_bench(dev)
+    paper_shapes = None if args.no_gram else paper_shapes_bench(dev)
     serving = (serving_bench(args.serving_requests, SEED, dev, local, sweep_of(args))
                if args.serving_requests else None)
     cpu = None if args.no_cpu_baseline else cpu_baseline(dev)
@@ -852,6 +917,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "e2e": e2e,
         "gram": gram,
+        "paper_shapes": paper_shapes,
         "other_passes": other,
         "alpha_fp32_scale": alpha,
         "fp32_scale": fp32_scale,
