@@ -581,6 +581,20 @@ def fp32_scale_bench(dev, evals=1000):
         ms = e0.elapsed_time(e1) / evals
         out["d%d" % d] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms,
                           "gbs_over_V": p * n * 4 / (ms / 1e3) / 1e9}
+    # the FP64 oracle on the host cores at the same workload: a slice of the samples, scaled by p
+    # (the evaluation is linear in p)
+    import oracle
+    ps = 1 << 17
+    Vt = np.ascontiguousarray(st["data"][:ps, :n].double().cpu().numpy().T)
+    lam0, A0 = models[0]
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < 4.0:
+        oracle.fg_implicit(None, Vt, lam0, A0, 3)
+        k += 1
+    per_full = (time.perf_counter() - t0) / k * (p / ps)
+    out["oracle_d3"] = {"evals_per_s": 1.0 / per_full, "cores": len(os.sched_getaffinity(0)),
+                        "sample": "%d of %d samples, %d evaluations in about 4 s, scaled by p"
+                                  % (ps, p, k)}
     del st
     return {"n": n, "p": p, "r": r, "dtype": "f32", "evals": evals, **out}
 
