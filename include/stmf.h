@@ -378,9 +378,11 @@ STMF_API stmf_status stmf_server_get_stats(stmf_server_t srv, stmf_server_stats*
  * is drawn inside the pass from Philox4x32-10 (Salmon et al., SC 2011) with counter
  * (l mod 2^32, l div 2^32, j, 0) and key (seed mod 2^32, seed div 2^32); the first two output
  * words give u1, u2 = (x + 1/2) 2^-32 and omega = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). FP64
- * samples: the draw, products and sums in FP64. Other samples: the draw and products in FP32 and
- * sums in FP32 over 16 tiles, folded into FP64 (about 1e-6 relative to the FP64 result); the
- * column normalisation is FP64.
+ * samples: the draw, products and sums in FP64 on the CUDA cores. BF16 and E4M3 samples with
+ * n <= 256 and r_hat <= 16: the tensor-core pass, the draw in FP32 as a BF16 hi/lo pair, FP32
+ * accumulation folded every 8 tiles. Other samples: the draw and products in FP32 on the CUDA
+ * cores, sums over 16 tiles folded into FP64. Either way about 1e-6 relative to the FP64 result;
+ * the column normalisation is FP64.
  *  V        samples (any type).     r_hat  1..64 columns (n * r_hat limited by shared memory).
  *  seed     key of the generator.   A0     device, n x r_hat FP64 column-major (out).
  * Enqueued on `stream`; asynchronous.
@@ -398,7 +400,9 @@ STMF_API stmf_status stmf_rrf_start(stmf_ctx_t ctx, const stmf_samples* V, int64
  * TTSVs X~ a^{d-1} are unbiased for X a^{d-1}. Arguments as for stmf_fg, plus
  *  idx   device, s int64 row indices in [0, V->p); an index outside that range reads as a zero
  *        sample and sets STMF_EINVAL in the device status word.
- * Runs on the CUDA cores (the pass gathers its rows). Enqueued on `stream`; asynchronous.
+ * BF16 and FP32 rows with n <= 256 and r <= 16 take the tensor-core passes, whose warps copy the
+ * rows into the pass's stages; other rows take the CUDA-core passes. Enqueued on `stream`;
+ * asynchronous.
  */
 STMF_API stmf_status stmf_fg_sampled(stmf_ctx_t ctx, const stmf_samples* V, const int64_t* idx, int64_t s,
                             int32_t d, int64_t r, const double* lambda, const double* A,
