@@ -381,7 +381,7 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=(), fixed_rate=80.0
     return out
 
 
-def other_passes_bench(st16, st32, lam_t, A_t, dev):
+def other_passes_bench(st16, st32, lam_t, A_t, dev, only=None):
     """The other passes over the samples, on the headline workload's samples (2^24 x 256): the
     range finder of eq. rrf (A0 = V Omega with r_hat = 16, Omega drawn inside the pass; one read
     of the BF16 V, CUDA cores) and the sampled evaluation of Sec. 5 (Lemma 5.1) on 2^20 rows
@@ -404,15 +404,17 @@ def other_passes_bench(st16, st32, lam_t, A_t, dev):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    ms_rrf = events(lambda: stmf.rrf_start(st16, 16, 7), 5)
-    gb_rrf = p * n * 2 / (ms_rrf / 1e3) / 1e9
+    out = {}
+    if only in (None, "rrf"):
+        ms_rrf = events(lambda: stmf.rrf_start(st16, 16, 7), 5)
+        gb_rrf = p * n * 2 / (ms_rrf / 1e3) / 1e9
+        out["rrf_start"] = {"n": n, "p": p, "r_hat": 16, "dtype": "bf16", "ms": ms_rrf,
+                            "gbs_over_V": gb_rrf, "frac_of_hbm": gb_rrf / peaks["hbm_gbs"]}
     s = 1 << 20
     idx = torch.randint(0, p, (s,), device=dev, dtype=torch.int64,
                         generator=torch.Generator(device=dev).manual_seed(SEED))
-    out = {"rrf_start": {"n": n, "p": p, "r_hat": 16, "dtype": "bf16", "ms": ms_rrf,
-                         "gbs_over_V": gb_rrf, "frac_of_hbm": gb_rrf / peaks["hbm_gbs"]}}
     for name, st, eb in (("sampled_fg_bf16", st16, 2), ("sampled_fg_f32", st32, 4)):
-        if st is None:
+        if st is None or only not in (None, name[len("sampled_fg_"):]):
             continue
         ms_smp = events(lambda: stmf.fg_sampled(st, idx, D, lam_t, A_t), 20)
         gb_smp = s * n * eb / (ms_smp / 1e3) / 1e9
@@ -709,6 +711,8 @@ def main():
                     help="run the Gaussian-mixture study grid of Sec. 4.2 (n=500) and print its line")
     ap.add_argument("--alpha-only", action="store_true",
                     help="only ||X||^2 from the distinct entries of X at n=100, p=2.5e6, d=3")
+    ap.add_argument("--other-passes-only", choices=["all", "rrf", "bf16", "f32"], default=None,
+                    help="time only the range finder and/or the sampled evaluation on --p samples")
     ap.add_argument("--paper-shapes-only", action="store_true",
                     help="time only Sec. 4.1's six scenarios (FP64) and print them")
     ap.add_argument("--gram-only", action="store_true",
@@ -736,6 +740,22 @@ def main():
     dev = torch.device("cuda", local)
     if args.paper_shapes_only:
         print(json.dumps(paper_shapes_bench(dev)), flush=True)
+        return
+    if args.other_passes_only:
+        import numpy as np
+        import torch
+
+        from paper_1911_03813_gb300 import inputs
+        which = None if args.other_passes_only == "all" else args.other_passes_only
+        st16 = (inputs.gmm_device(N_FEAT, args.p, N_MEANS, SIGMA, SEED, dev, out_dtype="bf16")
+                if which != "f32" else None)
+        st32 = (inputs.gmm_device(N_FEAT, args.p, N_MEANS, SIGMA, SEED, dev, out_dtype="f32")
+                if which in (None, "f32") else None)
+        lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
+        lam_t = torch.tensor(lam, device=dev)
+        A_t = torch.tensor(np.ascontiguousarray(A.T), device=dev).T
+        print(json.dumps(other_passes_bench(st16 if st16 is not None else st32, st32, lam_t, A_t,
+                                            dev, only=which)), flush=True)
         return
     if args.gram_only:
         print(json.dumps(gram_bench(dev)), flush=True)
