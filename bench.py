@@ -381,12 +381,12 @@ def serving_bench(n_requests, seed, dev, device_index, sweep=(), fixed_rate=80.0
     return out
 
 
-def other_passes_bench(st16, st32, lam_t, A_t, dev, only=None):
+def other_passes_bench(st16, st32, lam_t, A_t, dev, only=None, st8=None):
     """The other passes over the samples, on the headline workload's samples (2^24 x 256): the
     range finder of eq. rrf (A0 = V Omega with r_hat = 16, Omega drawn inside the pass; one read
     of the BF16 V, CUDA cores) and the sampled evaluation of Sec. 5 (Lemma 5.1) on 2^20 rows
-    gathered at random from the BF16 and the FP32 copy (CUDA-core gather passes), each against
-    the HBM copy peak over the bytes it reads."""
+    gathered at random from the BF16, the FP32 and the E4M3 copy (the tensor-core passes gather
+    them), each against the HBM copy peak over the bytes it reads."""
     import torch
 
     from paper_1911_03813_gb300 import stmf
@@ -413,11 +413,13 @@ def other_passes_bench(st16, st32, lam_t, A_t, dev, only=None):
     s = 1 << 20
     idx = torch.randint(0, p, (s,), device=dev, dtype=torch.int64,
                         generator=torch.Generator(device=dev).manual_seed(SEED))
-    for name, st, eb in (("sampled_fg_bf16", st16, 2), ("sampled_fg_f32", st32, 4)):
+    for name, st, eb in (("sampled_fg_bf16", st16, 2), ("sampled_fg_f32", st32, 4),
+                         ("sampled_fg_e4m3", st8, 1)):
         if st is None or only not in (None, name[len("sampled_fg_"):]):
             continue
         ms_smp = events(lambda: stmf.fg_sampled(st, idx, D, lam_t, A_t), 20)
-        gb_smp = s * n * eb / (ms_smp / 1e3) / 1e9
+        row_bytes = n * eb + (4 if name.endswith("e4m3") else 0)  # E4M3: codes and the scale
+        gb_smp = s * row_bytes / (ms_smp / 1e3) / 1e9
         out[name] = {"n": n, "rows": s, "r": R, "d": D, "ms": ms_smp, "gbs_over_rows": gb_smp,
                      "frac_of_hbm": gb_smp / peaks["hbm_gbs"], "row_draw": "uniform, with replacement"}
     return out
@@ -711,7 +713,8 @@ def main():
                     help="run the Gaussian-mixture study grid of Sec. 4.2 (n=500) and print its line")
     ap.add_argument("--alpha-only", action="store_true",
                     help="only ||X||^2 from the distinct entries of X at n=100, p=2.5e6, d=3")
-    ap.add_argument("--other-passes-only", choices=["all", "rrf", "bf16", "f32"], default=None,
+    ap.add_argument("--other-passes-only", choices=["all", "rrf", "bf16", "f32", "e4m3"],
+                    default=None,
                     help="time only the range finder and/or the sampled evaluation on --p samples")
     ap.add_argument("--paper-shapes-only", action="store_true",
                     help="time only Sec. 4.1's six scenarios (FP64) and print them")
@@ -748,14 +751,17 @@ def main():
         from paper_1911_03813_gb300 import inputs
         which = None if args.other_passes_only == "all" else args.other_passes_only
         st16 = (inputs.gmm_device(N_FEAT, args.p, N_MEANS, SIGMA, SEED, dev, out_dtype="bf16")
-                if which != "f32" else None)
+                if which in (None, "rrf", "bf16") else None)
         st32 = (inputs.gmm_device(N_FEAT, args.p, N_MEANS, SIGMA, SEED, dev, out_dtype="f32")
                 if which in (None, "f32") else None)
+        st8 = (inputs.gmm_device(N_FEAT, args.p, N_MEANS, SIGMA, SEED, dev, out_dtype="e4m3")
+               if which in (None, "e4m3") else None)
         lam, A = inputs.random_model(N_FEAT, R, seed=SEED + 1)
         lam_t = torch.tensor(lam, device=dev)
         A_t = torch.tensor(np.ascontiguousarray(A.T), device=dev).T
-        print(json.dumps(other_passes_bench(st16 if st16 is not None else st32, st32, lam_t, A_t,
-                                            dev, only=which)), flush=True)
+        first = next(x for x in (st16, st32, st8) if x is not None)  # its p and n
+        print(json.dumps(other_passes_bench(st16 if st16 is not None else first, st32, lam_t,
+                                            A_t, dev, only=which, st8=st8)), flush=True)
         return
     if args.gram_only:
         print(json.dumps(gram_bench(dev)), flush=True)
@@ -908,7 +914,7 @@ def main():
 
     if rank != 0:
         return
-    other = None if args.no_gram else other_passes_bench(st16, st32, lam_t, A_t, dev)
+    other = None if args.no_gram else other_passes_bench(st16, st32, lam_t, A_t, dev, st8=st8)
     del st16, st32, st8
     torch.cuda.empty_cache()
     gram = None if args.no_gram else gram_bench(dev)

@@ -400,8 +400,8 @@ STMF_API stmf_status stmf_rrf_start(stmf_ctx_t ctx, const stmf_samples* V, int64
  * TTSVs X~ a^{d-1} are unbiased for X a^{d-1}. Arguments as for stmf_fg, plus
  *  idx   device, s int64 row indices in [0, V->p); an index outside that range reads as a zero
  *        sample and sets STMF_EINVAL in the device status word.
- * BF16 and FP32 rows with n <= 256 and r <= 16 take the tensor-core passes, whose warps copy the
- * rows into the pass's stages; other rows take the CUDA-core passes. Enqueued on `stream`;
+ * BF16, E4M3 and FP32 rows with n <= 256 and r <= 16 take the tensor-core passes, whose warps
+ * copy the rows into the pass's stages; FP64 rows take the CUDA-core pass. Enqueued on `stream`;
  * asynchronous.
  */
 STMF_API stmf_status stmf_fg_sampled(stmf_ctx_t ctx, const stmf_samples* V, const int64_t* idx, int64_t s,

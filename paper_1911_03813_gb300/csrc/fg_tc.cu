@@ -1,7 +1,8 @@
 // Fused pass over BF16 (and E4M3) samples on the 5th-generation tensor cores (tcgen05, TMA,
 // TMEM), with two more modes of the same pipeline: the randomized range finder of eq. rrf
 // (A0 = V Omega, Omega drawn in the epilogue, no MMA1) and the sampled evaluation of Sec. 5
-// (rows idx[0..p) copied into the stages by gather warps in place of TMA).
+// (rows idx[0..p) copied into the stages in place of TMA: by gather warps for BF16 samples, by
+// the converter warps for E4M3 samples).
 //
 // Computes, per persistent CTA and over that CTA's sample tiles, the partial sums of Alg. 2's
 // Y (Lemma 3.3, eq. Y) and of Lemma 3.5:
@@ -139,15 +140,15 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[C]) {
 //                 and no w; the epilogue draws row l of the Gaussian test matrix (Philox4x32-10,
 //                 FP32 Box-Muller; times s_l for E4M3) as W, and MMA2 accumulates V^T W as above.
 //                 MMA2 then waits for the staged tile itself, which MMA1 otherwise orders.
-// MODE = kGather: the sampled evaluation of Sec. 5 (Lemma 5.1) on rows idx[0..p) of BF16
-//                 samples: NCONV gather warps copy the rows into the stages in place of TMA.
+// MODE = kGather: the sampled evaluation of Sec. 5 (Lemma 5.1) on rows idx[0..p): for BF16
+//                 samples NCONV gather warps copy the rows into the stages in place of TMA; for
+//                 E4M3 samples the converter warps fetch the code rows before widening them.
 enum PassMode { kFused = 0, kRrf = 1, kGather = 2 };
 
 template <int RP, bool FP8, int MODE>
 __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHREADS, 1)
     fg_tc_kernel(const __grid_constant__ CUtensorMap tmap, const FgParams prm, const TcExtra ex) {
   constexpr bool RRF = MODE == kRrf, GATHER = MODE == kGather;
-  static_assert(!(GATHER && FP8), "gathered rows: BF16 samples");
   constexpr int NT = (FP8 || GATHER) ? NTHREADS_FP8 : NTHREADS;
   using C = Cfg<RP>;
   constexpr int N = C::N;
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHR
       tc::mma_commit(&mma_done[1]);
       tc::mbar_wait(&mma_done[1], 0, &no_abort, WAIT_LIMIT);
     }
-  } else if (GATHER && warp >= 3 + NEPI / 32) {
+  } else if (GATHER && !FP8 && warp >= 3 + NEPI / 32) {
     // ------------------------------------------------------------------ row gather (Sec. 5)
     // Gather warp G copies rows y = G + 4k (k = 0..31) of tile t: row y is sample idx[t TM + y],
     // and one warp instruction copies the whole row, lane l taking its 16-byte chunk l (features
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHR
     // cp.async writes through the generic proxy, so each thread waits for its own copies and
     // fences them to the async proxy (the MMAs) before its warp arrives; two tiles are in flight
     // per warp, and the row indices are read one tile ahead (one per lane).
-    if constexpr (GATHER) {
+    if constexpr (GATHER && !FP8) {
       const int G = warp - (3 + NEPI / 32);  // 0 .. NCONV - 1
       const uint16_t* Vg = static_cast<const uint16_t*>(prm.V);
       const int lg = lane >> 3, lc = lane & 7;  // this lane's region and chunk of a row
@@ -429,13 +430,7 @@ __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHR
       // thread touches row y, so nothing else can read the bytes it overwrites.
       const int ct = tid - (96 + NEPI);
       const int y = ct;
-      bool ok = true;
-      for (int it = 0; it < my_tiles; ++it) {
-        const int st = it % S;
-        if (!tc::mbar_wait(&full[st], (it / S) & 1, abortv, WAIT_LIMIT)) {
-          ok = false;
-          break;
-        }
+      auto widen_row = [&](int st) {  // row y of stage st, in place
         unsigned char* stg = sV + size_t(st) * stage_bytes;
         for (int g = 0; g < nq; ++g) {
           unsigned char* lo = stg + size_t(2 * g) * REG_BYTES + y * 128;
@@ -464,9 +459,84 @@ __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHR
             }
           }
         }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&conv[st]);
+      };
+      bool ok = true;
+      if constexpr (GATHER) {
+        // Sampled E4M3 rows (Sec. 5): the converter warps fetch the code rows themselves. Warp w
+        // holds rows y = 32 w + l of every tile (lane l: the row index of sample y, read one
+        // tile ahead); one warp instruction copies two rows' codes (lanes 0-15 and 16-31,
+        // 16-byte chunk q = codes 16q .. 16q + 15: half q / 8 into region 2 (q / 8) + 1, chunk
+        // q % 8 at position (q % 8) ^ (y & 7), where TMA would put it), zero-filling codes past
+        // n and rows past p; a row outside the storage reads as zero and sets STMF_EINVAL. Tile
+        // t + 1 is requested before tile t is widened: each thread waits for its own copies of
+        // t, the warp syncs (its rows are complete), every thread widens its row in place,
+        // fences to the async proxy, and the warp arrives.
+        const int w = y >> 5, half = lane >> 4, q = lane & 15;
+        const bool active = (q >> 3) < nq;
+        const uint8_t* V8 = static_cast<const uint8_t*>(prm.V);
+        const int f = 16 * q;
+        const int fv = n - f >= 16 ? 16 : (n - f > 0 ? n - f : 0);
+        auto row_of = [&](int it_) -> int64_t {
+          const int64_t pos = (blockIdx.x + int64_t(it_) * gridDim.x) * TM + y;
+          if (it_ >= my_tiles || pos >= prm.p) return -1;
+          const int64_t row = prm.idx[pos];
+          if (row < 0 || row >= prm.rows) {
+            stmf_set_status(prm.status, STMF_EINVAL);
+            return -1;
+          }
+          return row;
+        };
+        auto finish = [&](int k) {
+          __syncwarp();
+          widen_row(k % S);
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&conv[k % S]);
+        };
+        int64_t row_cur = -1, row_next = row_of(0);
+        int it = 0;
+        for (; it < my_tiles; ++it) {
+          const int st = it % S;
+          ok = tc::mbar_wait(&empty[st], ((it / S) & 1) ^ 1, abortv, WAIT_LIMIT);
+          if (!__all_sync(0xffffffffu, ok)) {
+            ok = false;
+            break;
+          }
+          row_cur = row_next;
+          row_next = row_of(it + 1);
+          const uint32_t base = tc::smem_addr(sV + size_t(st) * stage_bytes) +
+                                uint32_t(2 * (q >> 3) + 1) * REG_BYTES;
+#pragma unroll 4
+          for (int i = 0; i < 16; ++i) {
+            const int yy = 32 * w + 2 * i + half;
+            const int64_t row = __shfl_sync(0xffffffffu, row_cur, 2 * i + half);
+            if (active) {
+              const int nb = row < 0 ? 0 : fv;
+              const uint8_t* src = nb ? V8 + row * prm.ld + f : V8;
+              cp_async16(base + uint32_t(yy) * 128u + ((uint32_t(q & 7) ^ uint32_t(yy & 7)) << 4),
+                         src, uint32_t(nb));
+            }
+          }
+          cp_async_commit();
+          if (it >= 1) {
+            cp_async_wait<1>();
+            finish(it - 1);
+          }
+        }
+        cp_async_wait<0>();  // nothing of this thread's stays in flight past here
+        if (ok && it >= 1) finish(it - 1);
+      } else {
+        for (int it = 0; it < my_tiles; ++it) {
+          const int st = it % S;
+          if (!tc::mbar_wait(&full[st], (it / S) & 1, abortv, WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          widen_row(st);
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&conv[st]);
+        }
       }
       if (!ok) fail();
     }
@@ -528,7 +598,10 @@ __global__ void __launch_bounds__((FP8 || MODE == kGather) ? NTHREADS_FP8 : NTHR
       nu_next = 0.f;
       if (it_ < my_tiles && sidx_ < prm.p) {
         nu_next = prm.nu ? (float)prm.nu[sidx_] : (float)prm.nu_uniform;
-        if constexpr (FP8) sc_next = prm.scale[sidx_];
+        if constexpr (FP8) {  // a gathered sample's scale is its row's (zero for a bad row)
+          const int64_t srow = GATHER ? prm.idx[sidx_] : sidx_;
+          sc_next = (srow >= 0 && srow < (GATHER ? prm.rows : prm.p)) ? prm.scale[srow] : 0.f;
+        }
       }
     };
     load_weight(0);
@@ -751,7 +824,7 @@ namespace {
 template <int MODE>
 cudaError_t launch_tc(int dtype, const FgParams& prm, int grid, cudaStream_t s) {
   if (dtype != STMF_BF16 && dtype != STMF_E4M3) return cudaErrorNotSupported;
-  if (MODE == kGather && (dtype != STMF_BF16 || !prm.idx)) return cudaErrorNotSupported;
+  if (MODE == kGather && !prm.idx) return cudaErrorNotSupported;
   if (prm.p > (int64_t(1) << 31) - TM) return cudaErrorInvalidValue;
   EncodeFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
@@ -768,11 +841,9 @@ cudaError_t launch_tc(int dtype, const FgParams& prm, int grid, cudaStream_t s) 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const TcExtra ex = plan(prm.n, prm.r, fp8);
-  if constexpr (MODE != kGather) {
-    if (fp8) {
-      if (rp_of(prm.r) == 8) return launch_rp<8, true, MODE>(tmap, prm, ex, grid, s);
-      return launch_rp<16, true, MODE>(tmap, prm, ex, grid, s);
-    }
+  if (fp8) {
+    if (rp_of(prm.r) == 8) return launch_rp<8, true, MODE>(tmap, prm, ex, grid, s);
+    return launch_rp<16, true, MODE>(tmap, prm, ex, grid, s);
   }
   if (rp_of(prm.r) == 8) return launch_rp<8, false, MODE>(tmap, prm, ex, grid, s);
   return launch_rp<16, false, MODE>(tmap, prm, ex, grid, s);

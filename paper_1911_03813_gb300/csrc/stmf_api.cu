@@ -96,8 +96,8 @@ cudaError_t stmf::smem_limit(const void* kernel, int bytes) {
 bool stmf::plan_pass(int dtype, int n, int r, int64_t p, int num_sms, bool gather,
                      stmf::PassPlan* out, int min_tiles) {
   PassPlan pl{kPassSimt, 0};
-  if (gather && dtype == STMF_BF16 && fg_tc_supported(dtype, n, r)) {
-    // sampled BF16 rows: the tensor-core pass with warps gathering the rows in place of TMA
+  if (gather && fg_tc_supported(dtype, n, r)) {
+    // sampled BF16 / E4M3 rows: the tensor-core pass with warps gathering the rows
     pl = {kPassTcGather, fg_tc_grid(dtype, n, r, p, num_sms, min_tiles)};
   } else if (gather && fg_tc_sub_gather_supported(dtype, n, r)) {
     // sampled FP32 rows: the sub-stage pass, its converter warps fetching the rows

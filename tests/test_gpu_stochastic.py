@@ -12,7 +12,7 @@ from paper_1911_03813_gb300 import inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-5, "e4m3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -58,18 +58,25 @@ def test_fg_sampled_out_of_range_index_is_reported(stmf):
     assert stmf.default_context().device_status() == 1   # STMF_EINVAL
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("dtype", ["bf16", "f32", "e4m3"])
 @pytest.mark.parametrize("n,s,r", [(256, 30001, 16), (100, 5000, 10), (37, 129, 3)])
 def test_fg_sampled_tensor_cores(stmf, dtype, n, s, r):
-    """Rows gathered by the tensor-core passes (BF16: gather warps of the whole-tile pass; FP32:
-    the converter warps of the sub-stage pass fetch the rows before splitting them): several
-    tiles and a ragged last one, n = 100 and 37 ending inside a 16-byte chunk, rows drawn with
-    repeats; against the oracle on the stored values, normwise and entry by entry."""
+    """Rows gathered by the tensor-core passes (BF16: gather warps of the whole-tile pass; E4M3:
+    its converter warps fetch the code rows before widening them, each sample's scale taken
+    through the index; FP32: the converter warps of the sub-stage pass fetch the rows before
+    splitting them): several tiles and a ragged last one, n = 100 and 37 ending inside a 16-byte
+    chunk, rows drawn with repeats; against the oracle on the stored values, normwise and entry
+    by entry."""
     p, d = 60000, 4
     data = inputs.gmm(n, p, 8, 0.1, seed=n + s)
     st = inputs.to_storage(data["V"], dtype, device="cuda")
     bits = inputs.storage_bits(st)
-    Vd = formats.decode_bf16(bits) if dtype == "bf16" else np.asarray(bits, dtype=np.float64)
+    if dtype == "bf16":
+        Vd = formats.decode_bf16(bits)
+    elif dtype == "e4m3":
+        Vd = formats.dequantize_e4m3(bits, st["scale"].cpu().numpy())
+    else:
+        Vd = np.asarray(bits, dtype=np.float64)
     idx = np.random.default_rng(s).integers(0, p, size=s)
     lam, A = inputs.random_model(n, r, seed=s)
     f_ref, gl_ref, GA_ref = stochastic.fg_sampled(Vd.T, idx, lam, A, d)
